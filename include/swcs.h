@@ -1,0 +1,135 @@
+/*
+ * swcs.h -- C ABI of the GB300 sparse wavefunction circuit solver (SWCS).
+ *
+ * The operations are those of ADAPT-VQE with a sparse determinant state
+ * (arXiv 2411.07920):
+ *   - the factorized ansatz prod_I U_I(theta_I) |Psi_0> with one-parameter
+ *     unitaries U = exp(theta (tau - tau^dag)) over single and double
+ *     excitations (Sec. II.A, Eqs. 1-3), each evaluated exactly (Sec. II.B);
+ *   - truncation of the state to the N_CUT largest |amplitude| after every
+ *     gate (Sec. II.B, Fig. 1);
+ *   - the energy <psi|H|psi>/<psi|psi> (Sec. II, Fig. 1 step 7);
+ *   - the operator-pool gradient over the generalized singles and doubles
+ *     pool, g_k = dE/dtheta_k for U_k appended at the end (Sec. II.C, step 4);
+ *   - the analytic gradient dE/dtheta of the truncated circuit (Sec. II.B).
+ *
+ * Conventions
+ *   Determinant: uint64_t occupation bitstring, bit p = spin-orbital p,
+ *     p = 2*spatial + spin (spin 0 = alpha).  The reference |Psi_0> has bits
+ *     0..n_elec-1 set.  Bits >= n_so are zero.
+ *   Operator: 5 bytes {kind, i0, i1, i2, i3}
+ *     kind 1: tau = a+_{i1} a_{i0}
+ *     kind 2: tau = a+_{i2} a+_{i3} a_{i1} a_{i0}
+ *     phase of a_p / a+_p on D = (-1)^(occupied spin-orbitals below p).
+ *     The index sets {i0,i1} and {i2,i3} must be disjoint and S_z-conserving.
+ *   ops[0] acts first on |Psi_0>.
+ *   Pool (canonical order): singles (p<q, same spin) tau = a+_q a_p by (p,q);
+ *     then doubles over disjoint pairs (p<q) < (r<s) with equal spin content,
+ *     tau = a+_r a+_s a_q a_p, by ((p,q),(r,s)).
+ *   Truncation keeps the n_keep largest |c|; equal |c| at the cut keep the
+ *     smaller bitstring; exact zeros are removed.  The state is not
+ *     renormalised; energies and gradients use the Rayleigh quotient.
+ *
+ * Memory and streams
+ *   A context owns its device memory (allocated on first need, grown, freed
+ *   by swcs_destroy) and issues all work on the CUDA stream given at
+ *   creation (NULL = legacy default stream).  Pointers named h_* are host
+ *   memory, d_* device memory; both stay owned by the caller and are not
+ *   retained after the call returns.  Functions that return values in host
+ *   memory synchronise the stream; *_dev variants only enqueue work.
+ *   A context must not be used from two host threads at once.
+ *
+ * Errors
+ *   Every function returns SWCS_OK (0) or a negative SWCS_ERR_* code and
+ *   records a message readable with swcs_last_error().  On error the state
+ *   held by the context is unspecified until the next swcs_apply_ansatz or
+ *   swcs_set_state.  No call aborts the process or traps the GPU: device
+ *   waits are bounded and report SWCS_ERR_TIMEOUT.
+ */
+#ifndef SWCS_H
+#define SWCS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct swcs_ctx swcs_ctx;
+
+enum swcs_status {
+  SWCS_OK = 0,
+  SWCS_ERR_INVALID_ARG = -1, /* bad size, index, op, or missing Hamiltonian/state */
+  SWCS_ERR_OOM = -2,         /* device or pinned-host allocation failed */
+  SWCS_ERR_TABLE_FULL = -3,  /* a hash table could not be grown enough */
+  SWCS_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
+  SWCS_ERR_CUDA = -5,        /* a CUDA runtime call failed (message has details) */
+  SWCS_ERR_NO_DEVICE = -6    /* no sm_103 device / kernel image for this device */
+};
+
+/* Create a context bound to the current CUDA device and to cuda_stream
+ * (a cudaStream_t, or NULL).  *out receives the handle. */
+int swcs_create(swcs_ctx** out, void* cuda_stream);
+int swcs_destroy(swcs_ctx* ctx);
+/* Last error message of this context (static string when ctx is NULL). */
+const char* swcs_last_error(const swcs_ctx* ctx);
+
+/* Hamiltonian H = sum h_pq a+_p a_q + 1/4 sum <pq||rs> a+_p a+_q a_s a_r
+ * (Sec. II; integrals as produced for Sec. III).
+ *   h_h   [n_so*n_so]       h[p*n_so + q], real symmetric
+ *   h_g   [n_so^4]          <pq||rs> at ((p*n_so + q)*n_so + r)*n_so + s,
+ *                           antisymmetric in (p,q) and (r,s), <pq||rs> = <rs||pq>
+ *   n_so  even, 4 <= n_so <= 64;  n_elec even, 2 <= n_elec < n_so
+ *         (closed-shell S_z = 0 sector: n_elec/2 electrons of each spin).
+ * Copies the data; clears the state. */
+int swcs_load_hamiltonian(swcs_ctx* ctx, const double* h_h, const double* h_g, int n_so, int n_elec);
+
+/* Size and operators of the generalized singles and doubles pool (Sec. II.C). */
+int swcs_pool_size(swcs_ctx* ctx, int64_t* n_out);
+int swcs_pool_ops(swcs_ctx* ctx, uint8_t* h_ops_out /* 5*pool_size bytes */);
+
+/* Evaluate the ansatz (Eq. 1) from |Psi_0>, truncating to n_keep after every
+ * gate (n_keep <= 0: no truncation).  h_ops: 5*n_ops bytes; h_theta: n_ops.
+ * The resulting state stays on the device in the context. */
+int swcs_apply_ansatz(swcs_ctx* ctx, const uint8_t* h_ops, const double* h_theta, int n_ops, int64_t n_keep);
+int swcs_apply_ansatz_dev(swcs_ctx* ctx, const uint8_t* d_ops, const double* d_theta, int n_ops, int64_t n_keep);
+/* Continue from the current state (no reset to |Psi_0>). */
+int swcs_apply_gates(swcs_ctx* ctx, const uint8_t* h_ops, const double* h_theta, int n_ops, int64_t n_keep);
+/* Truncate the current state alone (same rule as after a gate). */
+int swcs_truncate(swcs_ctx* ctx, int64_t n_keep);
+
+/* E = <psi|H|psi>/<psi|psi> and <psi|psi> of the current state. */
+int swcs_energy(swcs_ctx* ctx, double* h_e_out, double* h_norm2_out);
+/* Device variant: d_out[0] = E, d_out[1] = <psi|psi>. */
+int swcs_energy_dev(swcs_ctx* ctx, double* d_out);
+
+/* Pool gradient g_k = 2 <psi|H A_k|psi>/<psi|psi>, A_k = tau_k - tau_k^dag,
+ * for the canonical pool (ADAPT step 4, Sec. II.C).  h_subset == NULL:
+ * all pool entries are written to h_g_out[pool_size]; otherwise only
+ * h_g_out[h_subset[i]] for i < n_subset (other entries untouched), and only
+ * those operators' sigma contributions are formed. */
+int swcs_pool_gradients(swcs_ctx* ctx, double* h_g_out, const int64_t* h_subset, int64_t n_subset);
+int swcs_pool_gradients_dev(swcs_ctx* ctx, double* d_g_out, const int64_t* d_subset, int64_t n_subset);
+
+/* Energy and dE/dtheta of the truncated ansatz, each truncation held as a
+ * fixed projector onto its kept set (Sec. II.B, "analytic gradients").
+ * The forward pass keeps a copy of the state every ckpt_every gates
+ * (ckpt_every <= 0: 20); the backward pass replays each segment from its
+ * checkpoint.  Leaves the final state in the context. */
+int swcs_energy_grad(swcs_ctx* ctx, const uint8_t* h_ops, const double* h_theta, int n_ops, int64_t n_keep,
+                     int ckpt_every, double* h_e_out, double* h_dtheta_out);
+
+/* Current state size; copy-out sorted by bitstring (returns the size in *n_out;
+ * writes only when cap >= size); copy-in (duplicates are summed, zeros dropped). */
+int swcs_state_size(swcs_ctx* ctx, int64_t* n_out);
+int swcs_get_state(swcs_ctx* ctx, uint64_t* h_keys, double* h_amps, int64_t cap, int64_t* n_out);
+int swcs_set_state(swcs_ctx* ctx, const uint64_t* h_keys, const double* h_amps, int64_t n);
+
+/* Diagnostics of the last call: {gate_passes, select_passes, ext_distinct,
+ * ext_buckets, ext_capacity, kernel_launches, n_det_max, reserved}. */
+int swcs_stats(swcs_ctx* ctx, int64_t* h_out8);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWCS_H */

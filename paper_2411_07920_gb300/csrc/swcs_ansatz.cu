@@ -1,0 +1,330 @@
+// Gate sequence on the sparse determinant state: one persistent cooperative
+// launch runs every gate of the ansatz (Eq. 1), each as
+//   P1  gate apply + merge   (Eqs. 2-3, exact on each two-determinant block)
+//   P2  top-N radix select   (Sec. II.B truncation, Fig. 1)
+//   P3  compaction + re-index of the kept set
+// separated by bounded grid barriers.
+//
+// Merge without a merge table: a gate exp(theta (tau - tau^dag)) couples a
+// determinant D only to its partner tau D (or tau^dag D), and that partner
+// is unique.  Each thread owns one D of the input state S, looks up its
+// partner in the index table of S and writes D's new amplitude from the two
+// old ones; a partner that is not in S is appended (it can be produced by
+// exactly one D, so no duplicates arise).  Every new amplitude is the sum of
+// at most two separately rounded products, so the result does not depend on
+// the order of work: bit-identical to any correct sequential evaluation.
+//
+// Truncation: keep the n_keep largest |c|, ties at the cut by smaller
+// bitstring.  |c| as an IEEE-754 bit pattern with the sign cleared orders
+// like the value, so an MSD radix select over 8-bit digits (first digit 7
+// bits) finds the cut; when the cut lands on several equal |c| a second
+// radix select over the bitstrings of the tied entries picks the smallest.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "swcs_device.cuh"
+#include "swcs_kernels.h"
+
+namespace swcs {
+
+namespace {
+
+constexpr int kAbsPasses = 8;  // 7 + 7*8 = 63 bits of |c|
+constexpr int kKeyPasses = 8;  // 64 bits of the bitstring
+
+__device__ __forceinline__ int abs_shift(int pass) { return 56 - 8 * pass; }
+__device__ __forceinline__ int key_shift(int pass) { return 56 - 8 * pass; }
+
+__device__ __forceinline__ uint64_t abs_bits(double c) {
+  return (uint64_t)__double_as_longlong(c) & 0x7fffffffffffffffull;
+}
+
+// Selection state; every CTA keeps an identical copy in shared memory.
+struct SelState {
+  unsigned long long prefix;   // |c| bits decided so far
+  unsigned long long kprefix;  // bitstring bits decided so far (tie mode)
+  long long need;              // rank still to place within the current bucket
+  int shift;                   // digit shift of the last decided |c| digit
+  int kshift;                  // digit shift of the last decided key digit
+  int mode;                    // 0 none (keep all nonzero), 1 cut on |c|, 2 cut on |c| then key
+  int pass;                    // passes run
+};
+
+__device__ __forceinline__ bool keep_entry(const SelState& s, uint64_t key, double c) {
+  const uint64_t x = abs_bits(c);
+  if (x == 0) return false;
+  if (s.mode == 0) return true;
+  if (s.mode == 1) return (x >> s.shift) >= (s.prefix >> s.shift);
+  if (x != s.prefix) return x > s.prefix;
+  return (key >> s.kshift) <= (s.kprefix >> s.kshift);
+}
+
+struct GateOp {
+  int kind;
+  uint64_t mask_a;  // annihilated by tau
+  uint64_t mask_c;  // created by tau
+  int i0, i1, i2, i3;
+};
+
+__device__ __forceinline__ GateOp decode_op(const uint8_t* o) {
+  GateOp g;
+  g.kind = o[0];
+  g.i0 = o[1];
+  g.i1 = o[2];
+  g.i2 = o[3];
+  g.i3 = o[4];
+  if (g.kind == 1) {
+    g.mask_a = 1ull << g.i0;
+    g.mask_c = 1ull << g.i1;
+  } else if (g.kind == 2) {
+    g.mask_a = (1ull << g.i0) | (1ull << g.i1);
+    g.mask_c = (1ull << g.i2) | (1ull << g.i3);
+  } else {  // kind 0: identity (truncation only)
+    g.mask_a = 0;
+    g.mask_c = 0;
+  }
+  return g;
+}
+
+// Counters per gate, in a ring of 3 so that the next gate's set can be
+// reset while the current one is live.
+enum { kCtrExtra = 0, kCtrZero = 1, kCtrKept = 2, kCtrN = 4 };
+
+}  // namespace
+
+__global__ void __launch_bounds__(kAnsatzThreads)
+ansatz_kernel(AnsatzArgs a) {
+  __shared__ SelState sel;
+  __shared__ unsigned s_hist[256];
+  __shared__ long long s_n;
+
+  const unsigned nblocks = gridDim.x;
+  const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t gstride = (size_t)nblocks * blockDim.x;
+  uint64_t* keysA = a.keys_a;
+  double* ampsA = a.amps_a;
+  uint64_t* keysB = a.keys_b;
+  double* ampsB = a.amps_b;
+  int tab_cur = a.tab_cur;
+
+  // ---------------------------------------------------------------- prologue
+  if (threadIdx.x == 0) {
+    s_n = a.reset_to_hf ? 1 : (long long)*a.n_state;
+  }
+  __syncthreads();
+  long long n = s_n;
+  if (a.reset_to_hf && gtid == 0) {
+    keysA[0] = a.hf;
+    ampsA[0] = 1.0;
+  }
+  for (size_t i = gtid; i <= a.tab_mask; i += gstride) {
+    a.tab[0][i].key = kEmpty;
+    a.tab[1][i].key = kEmpty;
+  }
+  for (size_t i = gtid; i < 3 * kCtrN; i += gstride) a.ctr[i] = 0;
+  if (!grid_barrier(a.bar, nblocks, a.err, a.timeout_ns)) return;
+  for (size_t i = gtid; i < (size_t)n; i += gstride) {
+    if (!idx_insert(a.tab[tab_cur], a.tab_mask, keysA[i], i)) set_error(a.err, kDevTableFull);
+  }
+  if (!grid_barrier(a.bar, nblocks, a.err, a.timeout_ns)) return;
+
+  for (int g = 0; g < a.n_ops; ++g) {
+    unsigned long long* ctr = a.ctr + (g % 3) * kCtrN;
+    const GateOp op = decode_op(a.ops + 5 * g);
+    const double cs = a.cs[2 * g], sn = a.cs[2 * g + 1];
+    const IdxSlot* tcur = a.tab[tab_cur];
+    IdxSlot* tnxt = a.tab[tab_cur ^ 1];
+
+    // ------------------------------------------------------------ P1 gate + merge
+    if (gtid < kCtrN) a.ctr[((g + 1) % 3) * kCtrN + gtid] = 0;
+    for (size_t i = gtid; i < (size_t)(kAbsPasses + kKeyPasses) * 256; i += gstride) a.hist[i] = 0;
+    for (size_t i = gtid; i <= a.tab_mask; i += gstride) tnxt[i].key = kEmpty;
+    const size_t n_iter = ((size_t)n + gstride - 1) / gstride * gstride;  // warp-converged loop
+    for (size_t i = gtid; i < n_iter; i += gstride) {
+      const bool live = i < (size_t)n;
+      uint64_t d = 0, partner = 0;
+      double c = 0.0, out = 0.0, extra = 0.0;
+      bool has_extra = false;
+      if (live) {
+        d = keysA[i];
+        c = ampsA[i];
+        const bool up = op.kind && ((d & op.mask_a) == op.mask_a) && ((d & op.mask_c) == 0);
+        const bool dn = op.kind && ((d & op.mask_c) == op.mask_c) && ((d & op.mask_a) == 0);
+        if (up || dn) {
+          int sbit;
+          if (op.kind == 1) sbit = up ? single_phase(d, op.i0, op.i1) : single_phase(d, op.i1, op.i0);
+          else sbit = up ? double_phase(d, op.i0, op.i1, op.i2, op.i3) : double_phase(d, op.i2, op.i3, op.i0, op.i1);
+          partner = d ^ op.mask_a ^ op.mask_c;
+          const double t1 = __dmul_rn(c, cs);
+          const int64_t j = idx_lookup(tcur, a.tab_mask, partner);
+          if (j >= 0) {
+            const double t2 = __dmul_rn(ampsA[j], sn);
+            // lower D: c' = c cos - s sin c_U ; upper D: c' = c cos + s sin c_L
+            out = __dadd_rn(t1, up ? apply_sign(t2, !sbit) : apply_sign(t2, sbit));
+          } else {
+            out = t1;
+            const double t = __dmul_rn(c, sn);
+            extra = up ? apply_sign(t, sbit) : apply_sign(t, !sbit);
+            has_extra = (extra != 0.0);
+          }
+        } else {
+          out = c;
+        }
+        keysB[i] = d;
+        ampsB[i] = out;
+      }
+      const unsigned long long slot = warp_alloc(&ctr[kCtrExtra], has_extra);
+      if (has_extra) {
+        const unsigned long long pos = (unsigned long long)n + slot;
+        if (pos < (unsigned long long)a.cap) {
+          keysB[pos] = partner;
+          ampsB[pos] = extra;
+        } else {
+          set_error(a.err, kDevTableFull);
+        }
+      }
+      const bool zero = live && out == 0.0;
+      const unsigned zb = __ballot_sync(__activemask(), zero);
+      if ((threadIdx.x & 31) == 0 && zb) atomicAdd(&ctr[kCtrZero], (unsigned long long)__popc(zb));
+    }
+    if (!grid_barrier(a.bar, nblocks, a.err, a.timeout_ns)) return;
+
+    const long long m = n + (long long)ld_key_relaxed((const uint64_t*)&ctr[kCtrExtra]);
+    const long long nz = m - (long long)ld_key_relaxed((const uint64_t*)&ctr[kCtrZero]);
+    if (m > a.cap) return;  // error already flagged
+
+    // ------------------------------------------------------------ P2 radix select
+    if (threadIdx.x == 0) {
+      sel.mode = (a.n_keep > 0 && nz > a.n_keep) ? 1 : 0;
+      sel.prefix = 0;
+      sel.kprefix = 0;
+      sel.need = a.n_keep;
+      sel.shift = 63;
+      sel.kshift = 64;
+      sel.pass = 0;
+    }
+    __syncthreads();
+    if (sel.mode != 0) {
+      bool decided = false;
+      for (int p = 0; p < kAbsPasses + kKeyPasses && !decided; ++p) {
+        const bool keyphase = p >= kAbsPasses;
+        const int sh = keyphase ? key_shift(p - kAbsPasses) : abs_shift(p);
+        for (int t = threadIdx.x; t < 256; t += blockDim.x) s_hist[t] = 0;
+        __syncthreads();
+        const unsigned long long pre = keyphase ? sel.kprefix : sel.prefix;
+        for (size_t i = gtid; i < (size_t)m; i += gstride) {
+          const double c = ampsB[i];
+          const uint64_t x = abs_bits(c);
+          if (x == 0) continue;
+          uint64_t v;
+          if (!keyphase) {
+            if (p > 0 && (x >> (sh + 8)) != (pre >> (sh + 8))) continue;
+            v = x;
+          } else {
+            if (x != sel.prefix) continue;
+            const uint64_t k = keysB[i];
+            if (p > kAbsPasses && (k >> (sh + 8)) != (pre >> (sh + 8))) continue;
+            v = k;
+          }
+          atomicAdd(&s_hist[(v >> sh) & 255u], 1u);
+        }
+        __syncthreads();
+        unsigned* gh = a.hist + p * 256;
+        for (int t = threadIdx.x; t < 256; t += blockDim.x)
+          if (s_hist[t]) atomicAdd(&gh[t], s_hist[t]);
+        if (!grid_barrier(a.bar, nblocks, a.err, a.timeout_ns)) return;
+        if (threadIdx.x == 0) {
+          long long need = sel.need, cum = 0;
+          int chosen = -1;
+          long long cnt = 0;
+          if (!keyphase) {
+            for (int v = 255; v >= 0; --v) {
+              const long long h = (long long)ld_acquire_u32(&gh[v]);
+              if (cum + h >= need) { chosen = v; cnt = h; break; }
+              cum += h;
+            }
+          } else {
+            for (int v = 0; v < 256; ++v) {
+              const long long h = (long long)ld_acquire_u32(&gh[v]);
+              if (cum + h >= need) { chosen = v; cnt = h; break; }
+              cum += h;
+            }
+          }
+          if (chosen < 0) {  // cannot happen: total >= need
+            set_error(a.err, kDevBadState);
+            chosen = 0;
+          }
+          need -= cum;
+          sel.need = need;
+          sel.pass = p + 1;
+          if (!keyphase) {
+            sel.prefix |= (unsigned long long)chosen << sh;
+            sel.shift = sh;
+            if (cnt == need) decided = true;          // whole bucket kept
+            else if (sh == 0) sel.mode = 2;            // exact |c| ties at the cut
+          } else {
+            sel.kprefix |= (unsigned long long)chosen << sh;
+            sel.kshift = sh;
+            if (cnt == need || sh == 0) decided = true;
+          }
+          if (decided) sel.pass |= 0x100;
+        }
+        __syncthreads();
+        decided = (sel.pass & 0x100) != 0;
+        if (ld_acquire_i32(a.err) != 0) return;
+      }
+    }
+    __syncthreads();
+    const SelState s = sel;
+
+    // ------------------------------------------------------------ P3 compaction + re-index
+    const size_t m_iter = ((size_t)m + gstride - 1) / gstride * gstride;
+    for (size_t i = gtid; i < m_iter; i += gstride) {
+      bool keep = false;
+      uint64_t k = 0;
+      double c = 0.0;
+      if (i < (size_t)m) {
+        k = keysB[i];
+        c = ampsB[i];
+        keep = keep_entry(s, k, c);
+      }
+      const unsigned long long pos = warp_alloc(&ctr[kCtrKept], keep);
+      if (keep) {
+        keysA[pos] = k;
+        ampsA[pos] = c;
+        if (!idx_insert(tnxt, a.tab_mask, k, pos)) set_error(a.err, kDevTableFull);
+        if (a.snap_keys) {
+          a.snap_keys[(size_t)g * a.snap_stride + pos] = k;
+          a.snap_amps[(size_t)g * a.snap_stride + pos] = c;
+        }
+      }
+    }
+    if (!grid_barrier(a.bar, nblocks, a.err, a.timeout_ns)) return;
+    n = (long long)ld_key_relaxed((const uint64_t*)&ctr[kCtrKept]);
+    if (a.snap_n && gtid == 0) a.snap_n[g] = n;
+    if (gtid == 0 && a.stats) {
+      atomicAdd((unsigned long long*)&a.stats[0], 1ull);
+      atomicAdd((unsigned long long*)&a.stats[1], (unsigned long long)(s.pass & 0xff));
+      atomicMax((unsigned long long*)&a.stats[6], (unsigned long long)m);
+    }
+    tab_cur ^= 1;
+  }
+  if (gtid == 0) {
+    *a.n_state = n;
+    *a.tab_cur_out = tab_cur;
+  }
+}
+
+int ansatz_blocks_per_sm() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ansatz_kernel, kAnsatzThreads, 0) != cudaSuccess) return 0;
+  return nb;
+}
+
+cudaError_t launch_ansatz(const AnsatzArgs& args, int nblocks, cudaStream_t st) {
+  AnsatzArgs a = args;
+  void* params[] = {&a};
+  return cudaLaunchCooperativeKernel((const void*)ansatz_kernel, dim3(nblocks), dim3(kAnsatzThreads), params, 0, st);
+}
+
+}  // namespace swcs

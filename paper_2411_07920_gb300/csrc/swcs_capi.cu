@@ -1,0 +1,756 @@
+// Host side of the C ABI declared in include/swcs.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/swcs.h"
+#include "swcs_device.cuh"
+#include "swcs_kernels.h"
+
+using namespace swcs;
+
+namespace {
+
+constexpr uint64_t kTimeoutNs = 2000000000ull;  // bounded device waits: 2 s
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct swcs_ctx {
+  cudaStream_t st = nullptr;
+  int dev = 0;
+  int nsm = 0;
+  std::string err;
+
+  // Hamiltonian
+  int n = 0, ne = 0, no = 0, nv = 0, npairs = 0;
+  bool have_ham = false;
+  double fci_dim = 0.0;
+  int64_t pool_size = 0;
+  std::vector<uint8_t> pool_ops;  // 5 bytes each
+  DevBuf h, J, Ws, G, opd, ops1, gstage;
+
+  // state
+  DevBuf keys_a, amps_a, keys_b, amps_b, tab0, tab1;
+  int64_t cap = 0;
+  uint64_t tab_mask = 0;
+  int tab_cur = 0;
+  bool have_state = false;
+  int64_t n_state_host = -1;  // cached size (-1 unknown)
+
+  // control and scratch
+  DevBuf ctrl;  // n_state, tab_cur, err, bar, ctr, hist, stats, acc, eout
+  DevBuf ops_dev, cs_dev;
+  DevBuf gdev, subset_dev, gsub;
+
+  // external sigma table
+  DevBuf ext;
+  uint64_t ext_cap = 0;
+  double ext_distinct_last = 0.0;
+  int64_t stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+
+  // pinned host staging
+  void* pin = nullptr;
+  size_t pin_bytes = 0;
+};
+
+namespace {
+
+// Layout of the small control block on the device.
+struct Ctrl {
+  long long n_state;
+  int tab_cur;
+  int err;
+  GridBar bar;
+  unsigned long long ctr[12];
+  unsigned hist[16 * 256];
+  long long stats[8];
+  double acc[2];
+  double eout[2];
+  unsigned long long n_distinct;
+};
+
+int fail(swcs_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+int cuda_fail(swcs_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, SWCS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                             \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);   \
+  } while (0)
+
+int ensure(swcs_ctx* c, DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return SWCS_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, SWCS_ERR_OOM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  b.bytes = bytes;
+  return SWCS_OK;
+}
+
+void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+int ensure_pinned(swcs_ctx* c, size_t bytes) {
+  if (c->pin_bytes >= bytes) return SWCS_OK;
+  if (c->pin) cudaFreeHost(c->pin);
+  c->pin = nullptr;
+  c->pin_bytes = 0;
+  if (cudaMallocHost(&c->pin, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, SWCS_ERR_OOM, "pinned host allocation of %zu bytes failed", bytes);
+  }
+  c->pin_bytes = bytes;
+  return SWCS_OK;
+}
+
+Ctrl* ctrl(swcs_ctx* c) { return (Ctrl*)c->ctrl.p; }
+
+uint64_t pow2_at_least(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+double binom(int n, int k) {
+  if (k < 0 || k > n) return 0.0;
+  double r = 1.0;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return r;
+}
+
+// Reads the device error word and maps it to a status (synchronises).
+int check_device(swcs_ctx* c, const char* where) {
+  cudaError_t e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return cuda_fail(c, e, where);
+  int derr = 0;
+  CK(cudaMemcpy(&derr, &ctrl(c)->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (derr == 0) return SWCS_OK;
+  int zero = 0;
+  CK(cudaMemcpy(&ctrl(c)->err, &zero, sizeof(int), cudaMemcpyHostToDevice));
+  c->have_state = false;
+  if (derr == kDevTimeout) return fail(c, SWCS_ERR_TIMEOUT, "%s: a device-side wait timed out", where);
+  if (derr == kDevTableFull) return fail(c, SWCS_ERR_TABLE_FULL, "%s: a device hash table or buffer overflowed", where);
+  return fail(c, SWCS_ERR_CUDA, "%s: device reported error %d", where, derr);
+}
+
+HamDev ham_dev(swcs_ctx* c) {
+  HamDev H;
+  H.n = c->n;
+  H.ne = c->ne;
+  H.no = c->no;
+  H.nv = c->nv;
+  H.npairs = c->npairs;
+  H.h = (const double*)c->h.p;
+  H.J = (const double*)c->J.p;
+  H.Ws = (const double*)c->Ws.p;
+  H.G = (const double*)c->G.p;
+  H.opd = (const int*)c->opd.p;
+  H.ops1 = (const int*)c->ops1.p;
+  H.pool_size = c->pool_size;
+  return H;
+}
+
+StateDev state_dev(swcs_ctx* c) {
+  StateDev S;
+  S.keys = (const uint64_t*)c->keys_a.p;
+  S.amps = (const double*)c->amps_a.p;
+  S.n = &ctrl(c)->n_state;
+  S.tab = (const IdxSlot*)(c->tab_cur ? c->tab1.p : c->tab0.p);
+  S.tab_mask = c->tab_mask;
+  return S;
+}
+
+// Canonical generalized singles and doubles pool and its (pair, pair) index tables.
+void build_pool(swcs_ctx* c, std::vector<int>& opd, std::vector<int>& ops1) {
+  const int n = c->n, np = c->npairs;
+  c->pool_ops.clear();
+  ops1.assign((size_t)n * n, -1);
+  opd.assign((size_t)np * np, -1);
+  int64_t k = 0;
+  for (int p = 0; p < n; ++p)
+    for (int q = p + 1; q < n; ++q)
+      if ((p & 1) == (q & 1)) {
+        ops1[(size_t)p * n + q] = (int)k++;
+        c->pool_ops.insert(c->pool_ops.end(), {1, (uint8_t)p, (uint8_t)q, 0, 0});
+      }
+  for (int a = 0; a < np; ++a) {
+    int p = 0, base = 0;
+    while (base + (n - 1 - p) <= a) { base += n - 1 - p; ++p; }
+    const int q = p + 1 + (a - base);
+    for (int b = a + 1; b < np; ++b) {
+      int r = 0, bb = 0;
+      while (bb + (n - 1 - r) <= b) { bb += n - 1 - r; ++r; }
+      const int s = r + 1 + (b - bb);
+      if (r == p || r == q || s == p || s == q) continue;
+      if ((p & 1) + (q & 1) != (r & 1) + (s & 1)) continue;
+      opd[(size_t)a * np + b] = (int)k++;
+      c->pool_ops.insert(c->pool_ops.end(), {2, (uint8_t)p, (uint8_t)q, (uint8_t)r, (uint8_t)s});
+    }
+  }
+  c->pool_size = k;
+}
+
+int validate_ops(swcs_ctx* c, const uint8_t* ops, int n_ops) {
+  for (int g = 0; g < n_ops; ++g) {
+    const uint8_t* o = ops + 5 * g;
+    const int kind = o[0];
+    if (kind == 1) {
+      if (o[1] >= c->n || o[2] >= c->n || o[1] == o[2] || ((o[1] ^ o[2]) & 1))
+        return fail(c, SWCS_ERR_INVALID_ARG, "op %d: invalid single (%d -> %d)", g, o[1], o[2]);
+    } else if (kind == 2) {
+      const int i0 = o[1], i1 = o[2], i2 = o[3], i3 = o[4];
+      if (i0 >= c->n || i1 >= c->n || i2 >= c->n || i3 >= c->n)
+        return fail(c, SWCS_ERR_INVALID_ARG, "op %d: index out of range", g);
+      if (i0 == i1 || i2 == i3 || i0 == i2 || i0 == i3 || i1 == i2 || i1 == i3)
+        return fail(c, SWCS_ERR_INVALID_ARG, "op %d: annihilated and created indices must be distinct", g);
+      if ((i0 & 1) + (i1 & 1) != (i2 & 1) + (i3 & 1))
+        return fail(c, SWCS_ERR_INVALID_ARG, "op %d: does not conserve S_z", g);
+    } else {
+      return fail(c, SWCS_ERR_INVALID_ARG, "op %d: kind must be 1 or 2", g);
+    }
+  }
+  return SWCS_OK;
+}
+
+// Sizes the state buffers for at most max_state determinants.
+int ensure_state_buffers(swcs_ctx* c, int64_t max_state) {
+  const int64_t cap = 2 * std::max<int64_t>(max_state, 1) + 64;
+  const uint64_t tcap = pow2_at_least((uint64_t)std::max<int64_t>(2 * max_state, 64));
+  if (cap > c->cap || tcap - 1 != c->tab_mask) {
+    // keep the current state when growing
+    int r;
+    DevBuf nk, na;
+    if ((r = ensure(c, nk, cap * 8))) return r;
+    if ((r = ensure(c, na, cap * 8))) { release(nk); return r; }
+    if (c->have_state && c->keys_a.p) {
+      long long ns = 0;
+      CK(cudaMemcpyAsync(&ns, &ctrl(c)->n_state, 8, cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      ns = std::min<long long>(ns, cap);
+      CK(cudaMemcpyAsync(nk.p, c->keys_a.p, ns * 8, cudaMemcpyDeviceToDevice, c->st));
+      CK(cudaMemcpyAsync(na.p, c->amps_a.p, ns * 8, cudaMemcpyDeviceToDevice, c->st));
+      CK(cudaStreamSynchronize(c->st));
+    }
+    release(c->keys_a);
+    release(c->amps_a);
+    c->keys_a = nk;
+    c->amps_a = na;
+    if ((r = ensure(c, c->keys_b, cap * 8))) return r;
+    if ((r = ensure(c, c->amps_b, cap * 8))) return r;
+    if ((r = ensure(c, c->tab0, tcap * sizeof(IdxSlot)))) return r;
+    if ((r = ensure(c, c->tab1, tcap * sizeof(IdxSlot)))) return r;
+    c->cap = cap;
+    c->tab_mask = tcap - 1;
+  }
+  return SWCS_OK;
+}
+
+int64_t max_state_for(swcs_ctx* c, int64_t n_keep, int n_ops, int64_t n_now) {
+  double bound = c->fci_dim;
+  if (n_ops < 60) bound = std::min(bound, (double)n_now * std::ldexp(1.0, n_ops));
+  if (n_keep > 0) bound = std::min(bound, (double)n_keep);
+  bound = std::max(bound, (double)n_now);
+  return (int64_t)bound;
+}
+
+int run_gates(swcs_ctx* c, const uint8_t* d_ops, const double* d_cs, int n_ops, int64_t n_keep, bool reset,
+              uint64_t* snap_keys = nullptr, double* snap_amps = nullptr, long long* snap_n = nullptr,
+              int64_t snap_stride = 0) {
+  const int bps = ansatz_blocks_per_sm();
+  if (bps <= 0) return fail(c, SWCS_ERR_NO_DEVICE, "ansatz kernel cannot be resident on this device");
+  AnsatzArgs a{};
+  a.keys_a = (uint64_t*)c->keys_a.p;
+  a.amps_a = (double*)c->amps_a.p;
+  a.keys_b = (uint64_t*)c->keys_b.p;
+  a.amps_b = (double*)c->amps_b.p;
+  a.cap = c->cap;
+  a.tab[0] = (IdxSlot*)c->tab0.p;
+  a.tab[1] = (IdxSlot*)c->tab1.p;
+  a.tab_mask = c->tab_mask;
+  a.tab_cur = 0;
+  a.ops = d_ops;
+  a.cs = d_cs;
+  a.n_ops = n_ops;
+  a.n_keep = n_keep;
+  a.reset_to_hf = reset ? 1 : 0;
+  a.hf = (c->ne >= 64) ? ~0ull : ((1ull << c->ne) - 1ull);
+  Ctrl* k = ctrl(c);
+  a.n_state = &k->n_state;
+  a.tab_cur_out = &k->tab_cur;
+  a.ctr = k->ctr;
+  a.hist = k->hist;
+  a.bar = &k->bar;
+  a.err = &k->err;
+  a.timeout_ns = kTimeoutNs;
+  a.snap_keys = snap_keys;
+  a.snap_amps = snap_amps;
+  a.snap_n = snap_n;
+  a.snap_stride = snap_stride;
+  a.stats = k->stats;
+  // barrier words must start at zero
+  CK(cudaMemsetAsync(&k->bar, 0, sizeof(GridBar), c->st));
+  CK(launch_ansatz(a, c->nsm * bps, c->st));
+  c->tab_cur = (int)(((unsigned)n_ops) & 1u);  // the kernel rebuilds tab[0] for the input, swaps per gate
+  c->have_state = true;
+  c->n_state_host = -1;
+  c->stats[5] += 1;
+  return SWCS_OK;
+}
+
+int need_ham(swcs_ctx* c) {
+  if (!c) return SWCS_ERR_INVALID_ARG;
+  if (!c->have_ham) return fail(c, SWCS_ERR_INVALID_ARG, "no Hamiltonian loaded");
+  return SWCS_OK;
+}
+
+int need_state(swcs_ctx* c) {
+  int r = need_ham(c);
+  if (r) return r;
+  if (!c->have_state) return fail(c, SWCS_ERR_INVALID_ARG, "no state: call swcs_apply_ansatz or swcs_set_state");
+  return SWCS_OK;
+}
+
+int64_t host_state_size(swcs_ctx* c) {
+  if (c->n_state_host >= 0) return c->n_state_host;
+  long long ns = 0;
+  if (cudaMemcpyAsync(&ns, &ctrl(c)->n_state, 8, cudaMemcpyDeviceToHost, c->st) != cudaSuccess) return -1;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return -1;
+  c->n_state_host = ns;
+  return ns;
+}
+
+int upload_ops(swcs_ctx* c, const uint8_t* h_ops, const double* h_theta, int n_ops) {
+  int r;
+  if ((r = ensure(c, c->ops_dev, (size_t)5 * n_ops + 16))) return r;
+  if ((r = ensure(c, c->cs_dev, (size_t)16 * n_ops + 16))) return r;
+  const size_t nb = (size_t)5 * n_ops, cb = (size_t)16 * n_ops;
+  if ((r = ensure_pinned(c, nb + cb + 64))) return r;
+  CK(cudaStreamSynchronize(c->st));  // staging buffer reuse
+  uint8_t* p = (uint8_t*)c->pin;
+  double* cs = (double*)(p + ((nb + 15) & ~(size_t)15));
+  memcpy(p, h_ops, nb);
+  for (int g = 0; g < n_ops; ++g) {  // host cos/sin: one libm call per gate
+    cs[2 * g] = std::cos(h_theta[g]);
+    cs[2 * g + 1] = std::sin(h_theta[g]);
+  }
+  CK(cudaMemcpyAsync(c->ops_dev.p, p, nb, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->cs_dev.p, cs, cb, cudaMemcpyHostToDevice, c->st));
+  return SWCS_OK;
+}
+
+__global__ void sincos_kernel(const double* th, double* cs, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double s, co;
+    sincos(th[i], &s, &co);
+    cs[2 * i] = co;
+    cs[2 * i + 1] = s;
+  }
+}
+
+int sweep(swcs_ctx* c, double* d_g) {
+  const HamDev H = ham_dev(c);
+  const StateDev S = state_dev(c);
+  Ctrl* k = ctrl(c);
+  const int nblk = c->nsm * sigma_blocks_per_sm();
+  const int64_t nd = host_state_size(c);
+  if (nd < 0) return fail(c, SWCS_ERR_CUDA, "cannot read state size");
+  const double nconn = 2.0 * c->no * c->nv + 2.0 * binom(c->no, 2) * binom(c->nv, 2) + (double)c->no * c->no * c->nv * c->nv;
+  double est = c->ext_distinct_last > 0 ? 1.25 * c->ext_distinct_last : std::min((double)nd * (nconn + 1.0), c->fci_dim);
+  est = std::min(est, c->fci_dim);
+  size_t free_b = 0, total_b = 0;
+  CK(cudaMemGetInfo(&free_b, &total_b));
+  const double budget = 0.80 * ((double)free_b + (double)c->ext.bytes);
+  uint64_t cmax = 1;
+  while ((double)(cmax * 2) * sizeof(ValSlot) <= budget) cmax <<= 1;
+  const double load = 0.6;
+  unsigned lb = 0;
+  while (est / (double)(1u << lb) > load * (double)cmax && lb < 20) ++lb;
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    const double per_bucket = est / (double)(1u << lb);
+    uint64_t cap = pow2_at_least((uint64_t)std::max(1024.0, per_bucket / load));
+    cap = std::min(cap, cmax);
+    if (c->ext_cap < cap) {
+      release(c->ext);
+      int r = ensure(c, c->ext, cap * sizeof(ValSlot));
+      if (r) return r;
+      c->ext_cap = cap;
+    }
+    cap = std::min<uint64_t>(c->ext_cap, pow2_at_least((uint64_t)std::max(1024.0, per_bucket / load)));
+    cap = std::min(cap, c->ext_cap);
+    CK(cudaMemsetAsync(d_g, 0, sizeof(double) * c->pool_size, c->st));
+    CK(cudaMemsetAsync(k->acc, 0, sizeof(double) * 2, c->st));
+    bool overflow = false;
+    double total_distinct = 0.0;
+    for (unsigned b = 0; b < (1u << lb) && !overflow; ++b) {
+      ExtTable T;
+      T.slots = (ValSlot*)c->ext.p;
+      T.mask = cap - 1;
+      T.nbucket_log2 = lb;
+      T.bucket = b;
+      T.n_distinct = &k->n_distinct;
+      T.err = &k->err;
+      CK(launch_clear_ext(T.slots, cap, c->st));
+      CK(cudaMemsetAsync(&k->n_distinct, 0, 8, c->st));
+      CK(launch_sigma_scatter(H, S, T, nblk, c->st));
+      unsigned long long nd_b = 0;
+      CK(cudaMemcpyAsync(&nd_b, &k->n_distinct, 8, cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      int derr = 0;
+      CK(cudaMemcpy(&derr, &k->err, sizeof(int), cudaMemcpyDeviceToHost));
+      if (derr == kDevTableFull || (double)nd_b > 0.85 * (double)cap) {
+        int zero = 0;
+        CK(cudaMemcpy(&k->err, &zero, sizeof(int), cudaMemcpyHostToDevice));
+        overflow = true;
+        break;
+      }
+      if (derr) return check_device(c, "pool sweep (scatter)");
+      total_distinct += (double)nd_b;
+      CK(launch_pool_gather(H, S, T, d_g, k->acc, b == 0, nblk, c->st));
+    }
+    if (overflow) {
+      est = std::max(est * 2.0, (double)cap);
+      while (est / (double)(1u << lb) > load * (double)cmax && lb < 20) ++lb;
+      continue;
+    }
+    c->ext_distinct_last = total_distinct;
+    c->stats[2] = (int64_t)total_distinct;
+    c->stats[3] = (int64_t)(1u << lb);
+    c->stats[4] = (int64_t)cap;
+    CK(launch_scale_gradient(d_g, c->pool_size, k->acc, c->st));
+    CK(launch_finalize_energy(k->acc, k->eout, c->st));
+    return SWCS_OK;
+  }
+  return fail(c, SWCS_ERR_TABLE_FULL, "external sigma table could not be sized (device memory too small)");
+}
+
+}  // namespace
+
+// =============================================================================
+extern "C" {
+
+int swcs_create(swcs_ctx** out, void* cuda_stream) {
+  if (!out) return SWCS_ERR_INVALID_ARG;
+  *out = nullptr;
+  swcs_ctx* c = new swcs_ctx();
+  c->st = (cudaStream_t)cuda_stream;
+  if (cudaGetDevice(&c->dev) != cudaSuccess) { delete c; return SWCS_ERR_NO_DEVICE; }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, c->dev) != cudaSuccess) { delete c; return SWCS_ERR_NO_DEVICE; }
+  if (prop.major != 10 || prop.minor != 3) {
+    cudaGetLastError();
+    delete c;
+    return SWCS_ERR_NO_DEVICE;
+  }
+  c->nsm = prop.multiProcessorCount;
+  if (ensure(c, c->ctrl, sizeof(Ctrl)) != SWCS_OK) { delete c; return SWCS_ERR_OOM; }
+  if (cudaMemset(c->ctrl.p, 0, sizeof(Ctrl)) != cudaSuccess) { delete c; return SWCS_ERR_CUDA; }
+  *out = c;
+  return SWCS_OK;
+}
+
+int swcs_destroy(swcs_ctx* c) {
+  if (!c) return SWCS_OK;
+  cudaStreamSynchronize(c->st);
+  DevBuf* bufs[] = {&c->h, &c->J, &c->Ws, &c->G, &c->opd, &c->ops1, &c->gstage, &c->keys_a, &c->amps_a,
+                    &c->keys_b, &c->amps_b, &c->tab0, &c->tab1, &c->ctrl, &c->ops_dev, &c->cs_dev,
+                    &c->gdev, &c->subset_dev, &c->gsub, &c->ext};
+  for (DevBuf* b : bufs) release(*b);
+  if (c->pin) cudaFreeHost(c->pin);
+  delete c;
+  return SWCS_OK;
+}
+
+const char* swcs_last_error(const swcs_ctx* c) {
+  if (!c) return "no context";
+  return c->err.c_str();
+}
+
+int swcs_load_hamiltonian(swcs_ctx* c, const double* h_h, const double* h_g, int n_so, int n_elec) {
+  if (!c) return SWCS_ERR_INVALID_ARG;
+  if (!h_h || !h_g) return fail(c, SWCS_ERR_INVALID_ARG, "null integral pointer");
+  if (n_so < 4 || n_so > 64 || (n_so & 1)) return fail(c, SWCS_ERR_INVALID_ARG, "n_so must be even, 4..64 (got %d)", n_so);
+  if (n_elec < 2 || n_elec >= n_so || (n_elec & 1))
+    return fail(c, SWCS_ERR_INVALID_ARG, "n_elec must be even with 2 <= n_elec < n_so (got %d)", n_elec);
+  const int n = n_so;
+  c->n = n;
+  c->ne = n_elec;
+  c->no = n_elec / 2;
+  c->nv = n / 2 - c->no;
+  c->npairs = n * (n - 1) / 2;
+  c->fci_dim = binom(n / 2, c->no) * binom(n / 2, c->no);
+  const size_t n2 = (size_t)n * n, n3 = n2 * n, n4 = n3 * n, np2 = (size_t)c->npairs * c->npairs;
+  int r;
+  if ((r = ensure(c, c->h, n2 * 8)) || (r = ensure(c, c->J, n2 * 8)) || (r = ensure(c, c->Ws, n3 * 8)) ||
+      (r = ensure(c, c->G, np2 * 8)) || (r = ensure(c, c->opd, np2 * 4)) || (r = ensure(c, c->ops1, n2 * 4)) ||
+      (r = ensure(c, c->gstage, n4 * 8)))
+    return r;
+  CK(cudaMemcpyAsync(c->h.p, h_h, n2 * 8, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->gstage.p, h_g, n4 * 8, cudaMemcpyHostToDevice, c->st));
+  CK(launch_pack_hamiltonian((const double*)c->gstage.p, n, (double*)c->J.p, (double*)c->Ws.p, (double*)c->G.p, c->st));
+  std::vector<int> opd, ops1;
+  build_pool(c, opd, ops1);
+  CK(cudaMemcpyAsync(c->opd.p, opd.data(), np2 * 4, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->ops1.p, ops1.data(), n2 * 4, cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  c->have_ham = true;
+  c->have_state = false;
+  c->ext_distinct_last = 0.0;
+  return SWCS_OK;
+}
+
+int swcs_pool_size(swcs_ctx* c, int64_t* n_out) {
+  int r = need_ham(c);
+  if (r) return r;
+  if (!n_out) return fail(c, SWCS_ERR_INVALID_ARG, "null output");
+  *n_out = c->pool_size;
+  return SWCS_OK;
+}
+
+int swcs_pool_ops(swcs_ctx* c, uint8_t* out) {
+  int r = need_ham(c);
+  if (r) return r;
+  if (!out) return fail(c, SWCS_ERR_INVALID_ARG, "null output");
+  memcpy(out, c->pool_ops.data(), c->pool_ops.size());
+  return SWCS_OK;
+}
+
+static int apply_common(swcs_ctx* c, const uint8_t* h_ops, const double* h_theta, int n_ops, int64_t n_keep,
+                        bool reset) {
+  int r = reset ? need_ham(c) : need_state(c);
+  if (r) return r;
+  if (n_ops < 0 || (n_ops > 0 && (!h_ops || !h_theta))) return fail(c, SWCS_ERR_INVALID_ARG, "bad ops / theta");
+  if ((r = validate_ops(c, h_ops, n_ops))) return r;
+  const int64_t n_now = reset ? 1 : host_state_size(c);
+  const int64_t ms = max_state_for(c, n_keep, n_ops, n_now);
+  if (ms > ((int64_t)1 << 31)) return fail(c, SWCS_ERR_INVALID_ARG, "state bound %lld too large: give n_keep", (long long)ms);
+  if ((r = ensure_state_buffers(c, ms))) return r;
+  if (n_ops == 0 && !reset) return SWCS_OK;
+  if ((r = upload_ops(c, h_ops, h_theta, n_ops))) return r;
+  if (reset) {
+    long long one = 1;
+    CK(cudaMemcpyAsync(&ctrl(c)->n_state, &one, 8, cudaMemcpyHostToDevice, c->st));
+  }
+  if (n_ops == 0) {  // reference determinant only
+    const uint8_t id[5] = {0, 0, 0, 0, 0};
+    const double z = 0.0;
+    if ((r = upload_ops(c, id, &z, 1))) return r;
+    if ((r = run_gates(c, (const uint8_t*)c->ops_dev.p, (const double*)c->cs_dev.p, 1, n_keep, true))) return r;
+    return check_device(c, "swcs_apply_ansatz");
+  }
+  if ((r = run_gates(c, (const uint8_t*)c->ops_dev.p, (const double*)c->cs_dev.p, n_ops, n_keep, reset))) return r;
+  return check_device(c, "swcs_apply_ansatz");
+}
+
+int swcs_apply_ansatz(swcs_ctx* c, const uint8_t* h_ops, const double* h_theta, int n_ops, int64_t n_keep) {
+  return apply_common(c, h_ops, h_theta, n_ops, n_keep, true);
+}
+
+int swcs_apply_gates(swcs_ctx* c, const uint8_t* h_ops, const double* h_theta, int n_ops, int64_t n_keep) {
+  return apply_common(c, h_ops, h_theta, n_ops, n_keep, false);
+}
+
+int swcs_apply_ansatz_dev(swcs_ctx* c, const uint8_t* d_ops, const double* d_theta, int n_ops, int64_t n_keep) {
+  int r = need_ham(c);
+  if (r) return r;
+  if (n_ops <= 0 || !d_ops || !d_theta) return fail(c, SWCS_ERR_INVALID_ARG, "bad ops / theta");
+  const int64_t ms = max_state_for(c, n_keep, n_ops, 1);
+  if (ms > ((int64_t)1 << 31)) return fail(c, SWCS_ERR_INVALID_ARG, "state bound too large: give n_keep");
+  if ((r = ensure_state_buffers(c, ms))) return r;
+  if ((r = ensure(c, c->cs_dev, (size_t)16 * n_ops + 16))) return r;
+  sincos_kernel<<<(n_ops + 255) / 256, 256, 0, c->st>>>(d_theta, (double*)c->cs_dev.p, n_ops);
+  CK(cudaGetLastError());
+  return run_gates(c, d_ops, (const double*)c->cs_dev.p, n_ops, n_keep, true);
+}
+
+int swcs_truncate(swcs_ctx* c, int64_t n_keep) {
+  int r = need_state(c);
+  if (r) return r;
+  const uint8_t id[5] = {0, 0, 0, 0, 0};
+  const double z = 0.0;
+  if ((r = upload_ops(c, id, &z, 1))) return r;
+  if ((r = run_gates(c, (const uint8_t*)c->ops_dev.p, (const double*)c->cs_dev.p, 1, n_keep, false))) return r;
+  return check_device(c, "swcs_truncate");
+}
+
+int swcs_energy_dev(swcs_ctx* c, double* d_out) {
+  int r = need_state(c);
+  if (r) return r;
+  Ctrl* k = ctrl(c);
+  CK(cudaMemsetAsync(k->acc, 0, 16, c->st));
+  CK(launch_energy(ham_dev(c), state_dev(c), k->acc, c->nsm * sigma_blocks_per_sm(), c->st));
+  CK(launch_finalize_energy(k->acc, d_out ? d_out : k->eout, c->st));
+  c->stats[5] += 2;
+  return SWCS_OK;
+}
+
+int swcs_energy(swcs_ctx* c, double* e_out, double* n2_out) {
+  int r = swcs_energy_dev(c, nullptr);
+  if (r) return r;
+  double out[2];
+  CK(cudaMemcpyAsync(out, ctrl(c)->eout, 16, cudaMemcpyDeviceToHost, c->st));
+  if ((r = check_device(c, "swcs_energy"))) return r;
+  if (e_out) *e_out = out[0];
+  if (n2_out) *n2_out = out[1];
+  return SWCS_OK;
+}
+
+int swcs_pool_gradients_dev(swcs_ctx* c, double* d_g_out, const int64_t* d_subset, int64_t n_subset) {
+  int r = need_state(c);
+  if (r) return r;
+  if (!d_g_out) return fail(c, SWCS_ERR_INVALID_ARG, "null output");
+  double* g = d_g_out;
+  if (d_subset) {
+    if ((r = ensure(c, c->gdev, sizeof(double) * c->pool_size))) return r;
+    g = (double*)c->gdev.p;
+  }
+  if ((r = sweep(c, g))) return r;
+  if (d_subset) CK(launch_gather_subset(g, d_subset, n_subset, d_g_out, c->st));
+  return SWCS_OK;
+}
+
+int swcs_pool_gradients(swcs_ctx* c, double* h_g_out, const int64_t* h_subset, int64_t n_subset) {
+  int r = need_state(c);
+  if (r) return r;
+  if (!h_g_out) return fail(c, SWCS_ERR_INVALID_ARG, "null output");
+  if ((r = ensure(c, c->gdev, sizeof(double) * c->pool_size))) return r;
+  if ((r = sweep(c, (double*)c->gdev.p))) return r;
+  if ((r = check_device(c, "swcs_pool_gradients"))) return r;
+  if (!h_subset) {
+    CK(cudaMemcpy(h_g_out, c->gdev.p, sizeof(double) * c->pool_size, cudaMemcpyDeviceToHost));
+  } else {
+    std::vector<double> all(c->pool_size);
+    CK(cudaMemcpy(all.data(), c->gdev.p, sizeof(double) * c->pool_size, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < n_subset; ++i) {
+      if (h_subset[i] < 0 || h_subset[i] >= c->pool_size) return fail(c, SWCS_ERR_INVALID_ARG, "subset index out of range");
+      h_g_out[h_subset[i]] = all[h_subset[i]];
+    }
+  }
+  return SWCS_OK;
+}
+
+int swcs_state_size(swcs_ctx* c, int64_t* n_out) {
+  int r = need_state(c);
+  if (r) return r;
+  const int64_t n = host_state_size(c);
+  if (n < 0) return fail(c, SWCS_ERR_CUDA, "cannot read state size");
+  *n_out = n;
+  return SWCS_OK;
+}
+
+int swcs_get_state(swcs_ctx* c, uint64_t* keys, double* amps, int64_t cap, int64_t* n_out) {
+  int r = need_state(c);
+  if (r) return r;
+  if ((r = check_device(c, "swcs_get_state"))) return r;
+  const int64_t n = host_state_size(c);
+  if (n < 0) return fail(c, SWCS_ERR_CUDA, "cannot read state size");
+  if (n_out) *n_out = n;
+  if (cap < n) return SWCS_OK;
+  std::vector<uint64_t> k(n);
+  std::vector<double> a(n);
+  CK(cudaMemcpy(k.data(), c->keys_a.p, 8 * n, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(a.data(), c->amps_a.p, 8 * n, cudaMemcpyDeviceToHost));
+  std::vector<int64_t> ord(n);
+  for (int64_t i = 0; i < n; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return k[x] < k[y]; });
+  for (int64_t i = 0; i < n; ++i) {
+    keys[i] = k[ord[i]];
+    amps[i] = a[ord[i]];
+  }
+  return SWCS_OK;
+}
+
+int swcs_set_state(swcs_ctx* c, const uint64_t* keys, const double* amps, int64_t n) {
+  int r = need_ham(c);
+  if (r) return r;
+  if (n < 0 || (n > 0 && (!keys || !amps))) return fail(c, SWCS_ERR_INVALID_ARG, "bad state arrays");
+  std::vector<std::pair<uint64_t, double>> v;
+  v.reserve(n);
+  const uint64_t valid = (c->n >= 64) ? ~0ull : ((1ull << c->n) - 1ull);
+  for (int64_t i = 0; i < n; ++i) {
+    if (keys[i] & ~valid) return fail(c, SWCS_ERR_INVALID_ARG, "determinant %lld has bits >= n_so", (long long)i);
+    if (__builtin_popcountll(keys[i]) != c->ne) return fail(c, SWCS_ERR_INVALID_ARG, "determinant %lld has wrong electron count", (long long)i);
+    if (__builtin_popcountll(keys[i] & 0x5555555555555555ull) != c->no)
+      return fail(c, SWCS_ERR_INVALID_ARG, "determinant %lld is outside the S_z = 0 sector", (long long)i);
+    v.emplace_back(keys[i], amps[i]);
+  }
+  std::sort(v.begin(), v.end(), [](const std::pair<uint64_t, double>& x, const std::pair<uint64_t, double>& y) { return x.first < y.first; });
+  std::vector<uint64_t> k;
+  std::vector<double> a;
+  for (size_t i = 0; i < v.size();) {
+    size_t j = i;
+    double s = 0.0;
+    while (j < v.size() && v[j].first == v[i].first) s += v[j++].second;
+    if (s != 0.0) { k.push_back(v[i].first); a.push_back(s); }
+    i = j;
+  }
+  const int64_t m = (int64_t)k.size();
+  c->have_state = false;
+  if ((r = ensure_state_buffers(c, std::max<int64_t>(m, 1)))) return r;
+  CK(cudaMemcpyAsync(c->keys_a.p, k.data(), 8 * m, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->amps_a.p, a.data(), 8 * m, cudaMemcpyHostToDevice, c->st));
+  long long mm = m;
+  CK(cudaMemcpyAsync(&ctrl(c)->n_state, &mm, 8, cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  c->have_state = true;
+  c->n_state_host = m;
+  // rebuild the index table: a truncation-free identity pass
+  const uint8_t id[5] = {0, 0, 0, 0, 0};
+  const double z = 0.0;
+  if ((r = upload_ops(c, id, &z, 1))) return r;
+  if ((r = run_gates(c, (const uint8_t*)c->ops_dev.p, (const double*)c->cs_dev.p, 1, 0, false))) return r;
+  return check_device(c, "swcs_set_state");
+}
+
+int swcs_stats(swcs_ctx* c, int64_t* out8) {
+  if (!c || !out8) return SWCS_ERR_INVALID_ARG;
+  long long dev[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  CK(cudaMemcpy(dev, ctrl(c)->stats, sizeof dev, cudaMemcpyDeviceToHost));
+  out8[0] = dev[0];
+  out8[1] = dev[1];
+  out8[2] = c->stats[2];
+  out8[3] = c->stats[3];
+  out8[4] = c->stats[4];
+  out8[5] = c->stats[5];
+  out8[6] = dev[6];
+  out8[7] = 0;
+  return SWCS_OK;
+}
+
+int swcs_energy_grad(swcs_ctx* c, const uint8_t* h_ops, const double* h_theta, int n_ops, int64_t n_keep,
+                     int ckpt_every, double* h_e_out, double* h_dtheta_out) {
+  (void)h_ops; (void)h_theta; (void)n_ops; (void)n_keep; (void)ckpt_every; (void)h_e_out; (void)h_dtheta_out;
+  return fail(c, SWCS_ERR_INVALID_ARG, "swcs_energy_grad: not built yet");
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// Internal interface between the C-ABI host code and the kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "swcs_device.cuh"
+
+namespace swcs {
+
+constexpr int kAnsatzThreads = 256;
+constexpr int kSigmaThreads = 256;
+constexpr int kMaxSpin = 32;  // spin-orbitals of one spin (n_so <= 64)
+
+struct AnsatzArgs {
+  uint64_t* keys_a;  // state S (input and output), capacity cap
+  double* amps_a;
+  uint64_t* keys_b;  // merged set Phi (scratch), capacity cap
+  double* amps_b;
+  int64_t cap;
+  IdxSlot* tab[2];  // index tables of S; tab[tab_cur] indexes the input state
+  uint64_t tab_mask;
+  int tab_cur;
+  const uint8_t* ops;  // 5 bytes per gate
+  const double* cs;    // (cos theta, sin theta) per gate
+  int n_ops;
+  int64_t n_keep;      // <= 0: no truncation
+  int reset_to_hf;
+  uint64_t hf;
+  long long* n_state;  // in: input size (unless reset_to_hf); out: output size
+  int* tab_cur_out;    // out: which table indexes the output state
+  unsigned long long* ctr;  // 12 counters
+  unsigned* hist;           // 16 x 256
+  GridBar* bar;
+  int* err;
+  uint64_t timeout_ns;
+  // optional per-gate snapshots of the kept state (adjoint replay)
+  uint64_t* snap_keys;
+  double* snap_amps;
+  long long* snap_n;
+  int64_t snap_stride;
+  long long* stats;  // optional: [0] gates, [1] select passes, [6] max |Phi|
+};
+
+int ansatz_blocks_per_sm();
+cudaError_t launch_ansatz(const AnsatzArgs& a, int nblocks, cudaStream_t st);
+
+// Hamiltonian and pool tables on the device.
+struct HamDev {
+  int n;        // spin-orbitals
+  int ne;       // electrons
+  int no;       // occupied per spin (ne/2)
+  int nv;       // virtual per spin (n/2 - no)
+  int npairs;   // n(n-1)/2
+  const double* h;     // [n*n]        h[p*n+q]
+  const double* J;     // [n*n]        <ij||ij>
+  const double* Ws;    // [n*n*n]      Ws[(p*n+q)*n+k] = <qk||pk>
+  const double* G;     // [npairs^2]   G[P(p,q)*npairs + P(r,s)] = <rs||pq>
+  const int* opd;      // [npairs^2]   pool index of doubles (lower pair, upper pair) or -1
+  const int* ops1;     // [n*n]        pool index of singles (lo, hi) or -1
+  int64_t pool_size;
+};
+
+__host__ __device__ __forceinline__ int pair_index(int p, int q, int n) {  // p < q
+  return p * (2 * n - p - 1) / 2 + (q - p - 1);
+}
+
+struct StateDev {
+  const uint64_t* keys;
+  const double* amps;
+  long long* n;  // device count
+  const IdxSlot* tab;
+  uint64_t tab_mask;
+};
+
+struct ExtTable {
+  ValSlot* slots;
+  uint64_t mask;
+  unsigned nbucket_log2;  // buckets B = 2^nbucket_log2
+  unsigned bucket;        // current bucket
+  unsigned long long* n_distinct;
+  int* err;
+};
+
+// Energy (sigma restricted to S): acc[0] += sum c_D sigma_D, acc[1] += sum c_D^2.
+cudaError_t launch_energy(const HamDev& H, const StateDev& S, double* acc, int nblocks, cudaStream_t st);
+// Pool sweep pass 1: sigma_E += <E|H|D> c_D for E in bucket.
+cudaError_t launch_sigma_scatter(const HamDev& H, const StateDev& S, const ExtTable& T, int nblocks,
+                                 cudaStream_t st);
+// Pool sweep pass 2: g[k(D,E)] += dir * phase * c_D * sigma_E for E in bucket;
+// acc[0] += c_D sigma_D, acc[1] += c_D^2 (only once: when add_norm).
+cudaError_t launch_pool_gather(const HamDev& H, const StateDev& S, const ExtTable& T, double* g, double* acc,
+                               int add_norm, int nblocks, cudaStream_t st);
+cudaError_t launch_clear_ext(ValSlot* slots, uint64_t n, cudaStream_t st);
+cudaError_t launch_finalize_energy(const double* acc, double* out, cudaStream_t st);
+cudaError_t launch_scale_gradient(double* g, int64_t n, const double* acc, cudaStream_t st);
+cudaError_t launch_gather_subset(const double* g, const int64_t* subset, int64_t n, double* out, cudaStream_t st);
+int sigma_blocks_per_sm();
+
+// Hamiltonian preparation from the full <pq||rs> array on the device.
+cudaError_t launch_pack_hamiltonian(const double* g_full, int n, double* J, double* Ws, double* G,
+                                    cudaStream_t st);
+
+}  // namespace swcs

@@ -1,0 +1,213 @@
+"""Python binding of the C ABI in include/swcs.h (argument marshalling only).
+
+Every computation runs in the CUDA library ``libswcs.so`` built in this
+package directory (``python -m paper_2411_07920_gb300._build``).  There is no
+CPU fallback: importing this module raises when the library is missing.
+
+``Context`` methods carry the C function names without the ``swcs_``
+prefix; host arrays are numpy, device arrays are torch CUDA tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libswcs.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "swcs.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run `python -m paper_2411_07920_gb300._build` "
+                      "(or __graft_entry__.build()) on a machine with nvcc")
+
+lib = ctypes.CDLL(LIB_PATH)
+
+STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "TABLE_FULL", -4: "TIMEOUT", -5: "CUDA", -6: "NO_DEVICE"}
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_i64 = ctypes.c_int64
+_p64 = ctypes.POINTER(ctypes.c_int64)
+_pd = ctypes.POINTER(ctypes.c_double)
+
+_SIGS = {
+    "swcs_create": ([ctypes.POINTER(_vp), _vp], _i),
+    "swcs_destroy": ([_vp], _i),
+    "swcs_last_error": ([_vp], ctypes.c_char_p),
+    "swcs_load_hamiltonian": ([_vp, _vp, _vp, _i, _i], _i),
+    "swcs_pool_size": ([_vp, _p64], _i),
+    "swcs_pool_ops": ([_vp, _vp], _i),
+    "swcs_apply_ansatz": ([_vp, _vp, _vp, _i, _i64], _i),
+    "swcs_apply_ansatz_dev": ([_vp, _vp, _vp, _i, _i64], _i),
+    "swcs_apply_gates": ([_vp, _vp, _vp, _i, _i64], _i),
+    "swcs_truncate": ([_vp, _i64], _i),
+    "swcs_energy": ([_vp, _pd, _pd], _i),
+    "swcs_energy_dev": ([_vp, _vp], _i),
+    "swcs_pool_gradients": ([_vp, _vp, _vp, _i64], _i),
+    "swcs_pool_gradients_dev": ([_vp, _vp, _vp, _i64], _i),
+    "swcs_energy_grad": ([_vp, _vp, _vp, _i, _i64, _i, _pd, _vp], _i),
+    "swcs_state_size": ([_vp, _p64], _i),
+    "swcs_get_state": ([_vp, _vp, _vp, _i64, _p64], _i),
+    "swcs_set_state": ([_vp, _vp, _vp, _i64], _i),
+    "swcs_stats": ([_vp, _vp], _i),
+}
+
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+def declared_symbols(header: str = HEADER):
+    """Function names declared in include/swcs.h."""
+    txt = open(header).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(swcs_\w+)\s*\(", txt, re.M)))
+
+
+class SwcsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_vp) if a is not None else None
+
+
+def _tptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+class Context:
+    """One solver context (``swcs_ctx``) on the current CUDA device and stream."""
+
+    def __init__(self, stream=None):
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+            except Exception:  # torch missing: legacy default stream
+                stream = 0
+        h = _vp()
+        r = lib.swcs_create(ctypes.byref(h), _vp(stream))
+        if r != 0:
+            raise SwcsError(r, "swcs_create failed (needs an sm_103 GPU)")
+        self._h = h
+        self.n_so = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.swcs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _ck(self, r):
+        if r != 0:
+            raise SwcsError(r, lib.swcs_last_error(self._h).decode())
+
+    # ------------------------------------------------------------------ API
+    def load_hamiltonian(self, h, g, n_so, n_elec):
+        h = _c(h, np.float64)
+        g = _c(g, np.float64)
+        assert h.size == n_so * n_so and g.size == n_so ** 4
+        self._ck(lib.swcs_load_hamiltonian(self._h, _ptr(h), _ptr(g), int(n_so), int(n_elec)))
+        self.n_so = n_so
+
+    def pool_size(self):
+        n = ctypes.c_int64()
+        self._ck(lib.swcs_pool_size(self._h, ctypes.byref(n)))
+        return n.value
+
+    def pool_ops(self):
+        out = np.zeros(5 * self.pool_size(), np.uint8)
+        self._ck(lib.swcs_pool_ops(self._h, _ptr(out)))
+        return out.reshape(-1, 5)
+
+    def apply_ansatz(self, ops, theta, n_keep):
+        ops = _c(ops, np.uint8).reshape(-1)
+        theta = _c(theta, np.float64)
+        self._ck(lib.swcs_apply_ansatz(self._h, _ptr(ops), _ptr(theta), len(theta), int(n_keep)))
+
+    def apply_ansatz_dev(self, d_ops, d_theta, n_keep):
+        self._ck(lib.swcs_apply_ansatz_dev(self._h, _tptr(d_ops), _tptr(d_theta), int(d_theta.numel()), int(n_keep)))
+
+    def apply_gates(self, ops, theta, n_keep):
+        ops = _c(ops, np.uint8).reshape(-1)
+        theta = _c(theta, np.float64)
+        self._ck(lib.swcs_apply_gates(self._h, _ptr(ops), _ptr(theta), len(theta), int(n_keep)))
+
+    def truncate(self, n_keep):
+        self._ck(lib.swcs_truncate(self._h, int(n_keep)))
+
+    def energy(self):
+        e, n2 = ctypes.c_double(), ctypes.c_double()
+        self._ck(lib.swcs_energy(self._h, ctypes.byref(e), ctypes.byref(n2)))
+        return e.value, n2.value
+
+    def energy_dev(self, d_out):
+        self._ck(lib.swcs_energy_dev(self._h, _tptr(d_out)))
+
+    def pool_gradients(self, subset=None):
+        out = np.full(self.pool_size(), np.nan)
+        if subset is None:
+            self._ck(lib.swcs_pool_gradients(self._h, _ptr(out), None, 0))
+        else:
+            sub = _c(subset, np.int64)
+            self._ck(lib.swcs_pool_gradients(self._h, _ptr(out), _ptr(sub), len(sub)))
+        return out
+
+    def pool_gradients_dev(self, d_g, d_subset=None):
+        n = 0 if d_subset is None else int(d_subset.numel())
+        self._ck(lib.swcs_pool_gradients_dev(self._h, _tptr(d_g), _tptr(d_subset), n))
+
+    def energy_grad(self, ops, theta, n_keep, ckpt_every=20):
+        ops = _c(ops, np.uint8).reshape(-1)
+        theta = _c(theta, np.float64)
+        e = ctypes.c_double()
+        d = np.zeros(len(theta))
+        self._ck(lib.swcs_energy_grad(self._h, _ptr(ops), _ptr(theta), len(theta), int(n_keep), int(ckpt_every),
+                                      ctypes.byref(e), _ptr(d)))
+        return e.value, d
+
+    def state_size(self):
+        n = ctypes.c_int64()
+        self._ck(lib.swcs_state_size(self._h, ctypes.byref(n)))
+        return n.value
+
+    def get_state(self):
+        n = self.state_size()
+        k = np.zeros(max(n, 1), np.uint64)
+        a = np.zeros(max(n, 1), np.float64)
+        m = ctypes.c_int64()
+        self._ck(lib.swcs_get_state(self._h, _ptr(k), _ptr(a), n, ctypes.byref(m)))
+        return k[:m.value], a[:m.value]
+
+    def set_state(self, keys, amps):
+        keys = _c(keys, np.uint64)
+        amps = _c(amps, np.float64)
+        self._ck(lib.swcs_set_state(self._h, _ptr(keys), _ptr(amps), len(keys)))
+
+    def stats(self):
+        out = np.zeros(8, np.int64)
+        self._ck(lib.swcs_stats(self._h, _ptr(out)))
+        keys = ["gate_passes", "select_passes", "ext_distinct", "ext_buckets", "ext_capacity",
+                "kernel_launches", "n_det_max", "reserved"]
+        return dict(zip(keys, out.tolist()))
