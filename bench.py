@@ -1,0 +1,315 @@
+#!/usr/bin/env python
+"""Benchmark: pool-gradient sweeps/s at 52 spin-orbitals / 12 electrons, N = 1e6.
+
+One step = one pass of the whole hot path on one synthetic workload:
+  apply the 200-gate ansatz from the reference determinant with top-1e6
+  truncation after every gate, the energy, and the full operator-pool
+  gradient (301,600 generalized singles and doubles).
+`value` is steps (= pool-gradient sweeps) per second with inputs resident in
+HBM; `e2e` is the same through the host-buffer C-ABI calls, host<->device
+copies included.  `--impl reference` times the CPU oracle on a bounded
+sample of the same workload instead.
+
+Multi-GPU (torchrun): every rank runs its own replica of the workload (the
+path has no exchange step), value = all ranks' sweeps / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pool-gradient sweeps/s at 52 spin-orbitals, 12 electrons, N=1e6"
+WORKLOAD = "so52_e12"
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="swcs", choices=["swcs", "reference"])
+    p.add_argument("--n-keep", type=int, default=1_000_000)
+    p.add_argument("--cpu-sample", type=int, default=400, help="determinants in the oracle's bounded sample")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        mx = [num(r[2]) for r in rows if num(r[2])]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        load = sorted(sm)[len(sm) // 2:] if sm else []
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ oracle sample
+def oracle_sample(w, n_sample, n_keep):
+    """Time the oracle's step on the same workload truncated to n_sample
+    determinants; scale by n_keep / n_sample (every part of the oracle's step
+    is linear in the state size at fixed orbitals)."""
+    import oracle as O
+    t0 = time.perf_counter()
+    k, a = O.apply_ansatz(w.n_so, w.n_e, w.ops, w.theta, n_sample)
+    O.energy(w.n_so, w.h, w.g, k, a)
+    O.pool_gradients(w.n_so, w.h, w.g, k, a)
+    dt = time.perf_counter() - t0
+    scale = n_keep / max(len(k), 1)
+    return dt, len(k), 1.0 / (dt * scale)
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2411_07920_gb300 import inputs as I
+    import oracle as O
+    O.build()
+    w = I.workload(WORKLOAD, n_keep=args.n_keep)
+    n_sample = min(args.cpu_sample, 100)
+    for _ in range(args.warmup):
+        oracle_sample(w, n_sample, args.n_keep)
+    total = 0.0
+    nk = 0
+    for _ in range(args.steps):
+        dt, nk, _ = oracle_sample(w, n_sample, args.n_keep)
+        total += dt
+    scale = args.n_keep / max(nk, 1)
+    sec_per_sweep = total / args.steps * scale
+    value = 1.0 / sec_per_sweep
+    sample = (f"oracle step (apply 200 gates, energy, full pool gradient) on the same 52/12 workload "
+              f"truncated to {nk} determinants, time x {scale:.0f} to N={args.n_keep}")
+    line = {"metric": METRIC, "value": value, "unit": "sweeps/s", "impl": "reference", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_per_sweep * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "52 spin-orbitals, 12 electrons, 200 gates, N=1e6, "
+                                                        "pool 301600 (seed 3)", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "sweeps/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_swcs(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2411_07920_gb300 import inputs as I
+    from paper_2411_07920_gb300 import swcs
+
+    w = I.workload(WORKLOAD, n_keep=args.n_keep)
+    ctx = swcs.Context()
+    ctx.load_hamiltonian(w.h, w.g, w.n_so, w.n_e)
+    pool = ctx.pool_size()
+    dev = torch.device("cuda", local)
+    d_ops = torch.from_numpy(w.ops.reshape(-1).copy()).to(dev)
+    d_theta = torch.from_numpy(w.theta.copy()).to(dev)
+    d_g = torch.empty(pool, dtype=torch.float64, device=dev)
+    d_e = torch.empty(2, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.apply_ansatz_dev(d_ops, d_theta, args.n_keep)
+        ctx.energy_dev(d_e)
+        ctx.pool_gradients_dev(d_g)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    ctx.profile_enable(True)
+    ctx.profile_read(reset=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the timed events)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        step()
+        ev1.record(stream)
+        ev1.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    stats = ctx.stats()
+    prof = ctx.profile_read(reset=True)
+    ctx.profile_enable(False)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = t.item()
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+
+    # ------------------------------------------------------------ roofline of the dominant kernel
+    import math
+    no, nv = w.n_e // 2, w.n_so // 2 - w.n_e // 2
+    n_conn = 2 * no * nv + 2 * math.comb(no, 2) * math.comb(nv, 2) + no * no * nv * nv
+    n_det = args.n_keep
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    dom_ms, dom_n = kinds[dom]
+    buckets = max(stats["ext_buckets"], 1)
+    pairs = n_det * (n_conn + 1)
+    per_pair = {"sigma_scatter": 24.0, "pool_gather": 16.0}
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    if dom in per_pair:
+        bytes_per_launch = per_pair[dom] * pairs / buckets
+    elif dom == "ansatz":
+        # per gate: read S (16 B/det), write and re-read Phi (32 B), select reads (8 B/pass), write S (16 B)
+        bytes_per_launch = (16 + 32 + 8 * max(stats["select_passes"] / max(stats["gates"], 1), 1) + 16) * \
+            stats["gate_dets"] / max(dom_n, 1)
+    else:
+        bytes_per_launch = 16.0 * pairs
+    achieved = bytes_per_launch / (dom_ms / dom_n / 1e3) / 1e9
+    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "traffic": None,
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    gate_ms = prof.get("ansatz", (0.0, 0))[0]
+    gate_dets_per_s = stats["gate_dets"] / (gate_ms / 1e3) if gate_ms > 0 else None
+    launches = int(sum(v[1] for v in prof.values()))
+
+    # ------------------------------------------------------------ end to end through the host API
+    e2e = None
+    if not args.no_e2e:
+        h_pin = torch.from_numpy(w.h.copy()).pin_memory()
+        g_pin = torch.from_numpy(w.g.reshape(-1).copy()).pin_memory()
+        ops_pin = torch.from_numpy(w.ops.reshape(-1).copy()).pin_memory()
+        th_pin = torch.from_numpy(w.theta.copy()).pin_memory()
+        h_np, g_np, ops_np, th_np = h_pin.numpy(), g_pin.numpy(), ops_pin.numpy(), th_pin.numpy()
+        t_e2e = 0.0
+        for it in range(1 + args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.load_hamiltonian(h_np, g_np, w.n_so, w.n_e)
+            ctx.apply_ansatz(ops_np, th_np, args.n_keep)
+            e_val, _ = ctx.energy()
+            g_host = ctx.pool_gradients()
+            dt = time.perf_counter() - t0
+            if it > 0:
+                t_e2e += dt
+        h2d = w.h.nbytes + w.g.nbytes + w.ops.nbytes + w.theta.nbytes
+        d2h = 16 + g_host.nbytes
+        e2e = {"value": world * args.steps / t_e2e, "unit": "sweeps/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle as O
+        O.build()
+        dt, nk, v = oracle_sample(w, args.cpu_sample, args.n_keep)
+        cpu = {"value": v, "unit": "sweeps/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle step (apply 200 gates, energy, full pool gradient) on the same workload "
+                         f"truncated to {nk} determinants ({dt:.1f} s), scaled x{args.n_keep / nk:.0f} to N={args.n_keep}"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
+                "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "52 spin-orbitals, 12 electrons, 200-gate ansatz (seed 3), "
+                                       f"N={args.n_keep}, GSD pool {pool}",
+                           "parallelism": f"replicas x{world}", "l2": "flushed between steps (512 MB write)"},
+                "gate_dets_per_s": gate_dets_per_s, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk,
+                "kernels_ms": {k: round(v[0], 3) for k, v in prof.items()},
+                "ext": {"distinct": stats["ext_distinct"], "buckets": stats["ext_buckets"],
+                        "capacity": stats["ext_capacity"]}}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_swcs(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -125,9 +125,21 @@ int swcs_state_size(swcs_ctx* ctx, int64_t* n_out);
 int swcs_get_state(swcs_ctx* ctx, uint64_t* h_keys, double* h_amps, int64_t cap, int64_t* n_out);
 int swcs_set_state(swcs_ctx* ctx, const uint64_t* h_keys, const double* h_amps, int64_t n);
 
-/* Diagnostics of the last call: {gate_passes, select_passes, ext_distinct,
- * ext_buckets, ext_capacity, kernel_launches, n_det_max, reserved}. */
+/* Diagnostics accumulated since the last swcs_profile_read(.., reset=1):
+ * {gates applied, radix-select passes, distinct determinants in the last
+ * external sigma table, its bucket count, its capacity, kernel launches,
+ * largest merged set |Phi|, sum over gates of the input state size
+ * (gate x determinant applications)}. */
 int swcs_stats(swcs_ctx* ctx, int64_t* h_out8);
+
+/* Per-kernel device time with CUDA events recorded on the context's stream
+ * around each launch (off by default).  Kinds: 0 gate/select kernel,
+ * 1 energy, 2 sigma scatter, 3 pool gather, 4 table clear, 5 other.
+ * swcs_profile_read synchronises, returns accumulated milliseconds and launch
+ * counts per kind (8 entries each; NULL to skip) and, when reset != 0,
+ * clears them together with the swcs_stats counters. */
+int swcs_profile_enable(swcs_ctx* ctx, int on);
+int swcs_profile_read(swcs_ctx* ctx, double* h_ms8, int64_t* h_launches8, int reset);
 
 #ifdef __cplusplus
 }

@@ -129,6 +129,7 @@ ansatz_kernel(AnsatzArgs a) {
   if (!grid_barrier(a.bar, nblocks, a.err, a.timeout_ns)) return;
 
   for (int g = 0; g < a.n_ops; ++g) {
+    const long long s_gate_in = n;
     unsigned long long* ctr = a.ctr + (g % 3) * kCtrN;
     const GateOp op = decode_op(a.ops + 5 * g);
     const double cs = a.cs[2 * g], sn = a.cs[2 * g + 1];
@@ -306,6 +307,7 @@ ansatz_kernel(AnsatzArgs a) {
       atomicAdd((unsigned long long*)&a.stats[0], 1ull);
       atomicAdd((unsigned long long*)&a.stats[1], (unsigned long long)(s.pass & 0xff));
       atomicMax((unsigned long long*)&a.stats[6], (unsigned long long)m);
+      atomicAdd((unsigned long long*)&a.stats[7], (unsigned long long)s_gate_in);
     }
     tab_cur ^= 1;
   }

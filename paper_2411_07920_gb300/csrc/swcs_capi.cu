@@ -62,6 +62,18 @@ struct swcs_ctx {
   // pinned host staging
   void* pin = nullptr;
   size_t pin_bytes = 0;
+
+  // per-kernel event timing (swcs_profile_*) and launch count
+  bool prof = false;
+  struct Ev {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Ev> ev_pending;
+  std::vector<cudaEvent_t> ev_free;
+  double prof_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t prof_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t launches = 0;
 };
 
 namespace {
@@ -135,6 +147,34 @@ int ensure_pinned(swcs_ctx* c, size_t bytes) {
 }
 
 Ctrl* ctrl(swcs_ctx* c) { return (Ctrl*)c->ctrl.p; }
+
+// Kernel kinds for swcs_profile_read.
+enum Kind { kKAnsatz = 0, kKEnergy = 1, kKScatter = 2, kKGather = 3, kKClear = 4, kKOther = 5 };
+
+cudaEvent_t take_event(swcs_ctx* c) {
+  if (!c->ev_free.empty()) {
+    cudaEvent_t e = c->ev_free.back();
+    c->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Launches one kernel through `launch`, counting it and, when profiling is
+// on, bracketing it with events on the context's stream.
+template <class F>
+cudaError_t launch_k(swcs_ctx* c, int kind, F&& launch) {
+  c->launches++;
+  if (!c->prof) return launch();
+  cudaEvent_t a = take_event(c), b = take_event(c);
+  if (a) cudaEventRecord(a, c->st);
+  cudaError_t e = launch();
+  if (b) cudaEventRecord(b, c->st);
+  if (a && b) c->ev_pending.push_back({kind, a, b});
+  return e;
+}
 
 uint64_t pow2_at_least(uint64_t x) {
   uint64_t p = 1;
@@ -320,11 +360,10 @@ int run_gates(swcs_ctx* c, const uint8_t* d_ops, const double* d_cs, int n_ops, 
   a.stats = k->stats;
   // barrier words must start at zero
   CK(cudaMemsetAsync(&k->bar, 0, sizeof(GridBar), c->st));
-  CK(launch_ansatz(a, c->nsm * bps, c->st));
+  CK(launch_k(c, kKAnsatz, [&] { return launch_ansatz(a, c->nsm * bps, c->st); }));
   c->tab_cur = (int)(((unsigned)n_ops) & 1u);  // the kernel rebuilds tab[0] for the input, swaps per gate
   c->have_state = true;
   c->n_state_host = -1;
-  c->stats[5] += 1;
   return SWCS_OK;
 }
 
@@ -420,9 +459,9 @@ int sweep(swcs_ctx* c, double* d_g) {
       T.bucket = b;
       T.n_distinct = &k->n_distinct;
       T.err = &k->err;
-      CK(launch_clear_ext(T.slots, cap, c->st));
+      CK(launch_k(c, kKClear, [&] { return launch_clear_ext(T.slots, cap, c->st); }));
       CK(cudaMemsetAsync(&k->n_distinct, 0, 8, c->st));
-      CK(launch_sigma_scatter(H, S, T, nblk, c->st));
+      CK(launch_k(c, kKScatter, [&] { return launch_sigma_scatter(H, S, T, nblk, c->st); }));
       unsigned long long nd_b = 0;
       CK(cudaMemcpyAsync(&nd_b, &k->n_distinct, 8, cudaMemcpyDeviceToHost, c->st));
       CK(cudaStreamSynchronize(c->st));
@@ -436,7 +475,7 @@ int sweep(swcs_ctx* c, double* d_g) {
       }
       if (derr) return check_device(c, "pool sweep (scatter)");
       total_distinct += (double)nd_b;
-      CK(launch_pool_gather(H, S, T, d_g, k->acc, b == 0, nblk, c->st));
+      CK(launch_k(c, kKGather, [&] { return launch_pool_gather(H, S, T, d_g, k->acc, b == 0, nblk, c->st); }));
     }
     if (overflow) {
       est = std::max(est * 2.0, (double)cap);
@@ -447,8 +486,8 @@ int sweep(swcs_ctx* c, double* d_g) {
     c->stats[2] = (int64_t)total_distinct;
     c->stats[3] = (int64_t)(1u << lb);
     c->stats[4] = (int64_t)cap;
-    CK(launch_scale_gradient(d_g, c->pool_size, k->acc, c->st));
-    CK(launch_finalize_energy(k->acc, k->eout, c->st));
+    CK(launch_k(c, kKOther, [&] { return launch_scale_gradient(d_g, c->pool_size, k->acc, c->st); }));
+    CK(launch_k(c, kKOther, [&] { return launch_finalize_energy(k->acc, k->eout, c->st); }));
     return SWCS_OK;
   }
   return fail(c, SWCS_ERR_TABLE_FULL, "external sigma table could not be sized (device memory too small)");
@@ -487,6 +526,8 @@ int swcs_destroy(swcs_ctx* c) {
                     &c->gdev, &c->subset_dev, &c->gsub, &c->ext};
   for (DevBuf* b : bufs) release(*b);
   if (c->pin) cudaFreeHost(c->pin);
+  for (auto& e : c->ev_pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+  for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
   delete c;
   return SWCS_OK;
 }
@@ -517,7 +558,7 @@ int swcs_load_hamiltonian(swcs_ctx* c, const double* h_h, const double* h_g, int
     return r;
   CK(cudaMemcpyAsync(c->h.p, h_h, n2 * 8, cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(c->gstage.p, h_g, n4 * 8, cudaMemcpyHostToDevice, c->st));
-  CK(launch_pack_hamiltonian((const double*)c->gstage.p, n, (double*)c->J.p, (double*)c->Ws.p, (double*)c->G.p, c->st));
+  CK(launch_k(c, kKOther, [&] { return launch_pack_hamiltonian((const double*)c->gstage.p, n, (double*)c->J.p, (double*)c->Ws.p, (double*)c->G.p, c->st); }));
   std::vector<int> opd, ops1;
   build_pool(c, opd, ops1);
   CK(cudaMemcpyAsync(c->opd.p, opd.data(), np2 * 4, cudaMemcpyHostToDevice, c->st));
@@ -588,8 +629,10 @@ int swcs_apply_ansatz_dev(swcs_ctx* c, const uint8_t* d_ops, const double* d_the
   if (ms > ((int64_t)1 << 31)) return fail(c, SWCS_ERR_INVALID_ARG, "state bound too large: give n_keep");
   if ((r = ensure_state_buffers(c, ms))) return r;
   if ((r = ensure(c, c->cs_dev, (size_t)16 * n_ops + 16))) return r;
-  sincos_kernel<<<(n_ops + 255) / 256, 256, 0, c->st>>>(d_theta, (double*)c->cs_dev.p, n_ops);
-  CK(cudaGetLastError());
+  CK(launch_k(c, kKOther, [&] {
+    sincos_kernel<<<(n_ops + 255) / 256, 256, 0, c->st>>>(d_theta, (double*)c->cs_dev.p, n_ops);
+    return cudaGetLastError();
+  }));
   return run_gates(c, d_ops, (const double*)c->cs_dev.p, n_ops, n_keep, true);
 }
 
@@ -608,9 +651,8 @@ int swcs_energy_dev(swcs_ctx* c, double* d_out) {
   if (r) return r;
   Ctrl* k = ctrl(c);
   CK(cudaMemsetAsync(k->acc, 0, 16, c->st));
-  CK(launch_energy(ham_dev(c), state_dev(c), k->acc, c->nsm * sigma_blocks_per_sm(), c->st));
-  CK(launch_finalize_energy(k->acc, d_out ? d_out : k->eout, c->st));
-  c->stats[5] += 2;
+  CK(launch_k(c, kKEnergy, [&] { return launch_energy(ham_dev(c), state_dev(c), k->acc, c->nsm * sigma_blocks_per_sm(), c->st); }));
+  CK(launch_k(c, kKOther, [&] { return launch_finalize_energy(k->acc, d_out ? d_out : k->eout, c->st); }));
   return SWCS_OK;
 }
 
@@ -635,7 +677,7 @@ int swcs_pool_gradients_dev(swcs_ctx* c, double* d_g_out, const int64_t* d_subse
     g = (double*)c->gdev.p;
   }
   if ((r = sweep(c, g))) return r;
-  if (d_subset) CK(launch_gather_subset(g, d_subset, n_subset, d_g_out, c->st));
+  if (d_subset) CK(launch_k(c, kKOther, [&] { return launch_gather_subset(g, d_subset, n_subset, d_g_out, c->st); }));
   return SWCS_OK;
 }
 
@@ -741,9 +783,44 @@ int swcs_stats(swcs_ctx* c, int64_t* out8) {
   out8[2] = c->stats[2];
   out8[3] = c->stats[3];
   out8[4] = c->stats[4];
-  out8[5] = c->stats[5];
+  out8[5] = c->launches;
   out8[6] = dev[6];
-  out8[7] = 0;
+  out8[7] = dev[7];
+  return SWCS_OK;
+}
+
+int swcs_profile_enable(swcs_ctx* c, int on) {
+  if (!c) return SWCS_ERR_INVALID_ARG;
+  c->prof = on != 0;
+  return SWCS_OK;
+}
+
+int swcs_profile_read(swcs_ctx* c, double* ms8, int64_t* n8, int reset) {
+  if (!c) return SWCS_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(c->st));
+  for (auto& e : c->ev_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
+      c->prof_ms[e.kind] += ms;
+      c->prof_n[e.kind] += 1;
+    }
+    c->ev_free.push_back(e.a);
+    c->ev_free.push_back(e.b);
+  }
+  c->ev_pending.clear();
+  for (int i = 0; i < 8; ++i) {
+    if (ms8) ms8[i] = c->prof_ms[i];
+    if (n8) n8[i] = c->prof_n[i];
+    if (reset) {
+      c->prof_ms[i] = 0;
+      c->prof_n[i] = 0;
+    }
+  }
+  if (reset) {
+    c->launches = 0;
+    long long z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    CK(cudaMemcpy(ctrl(c)->stats, z, sizeof z, cudaMemcpyHostToDevice));
+  }
   return SWCS_OK;
 }
 

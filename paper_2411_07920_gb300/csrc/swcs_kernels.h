@@ -38,7 +38,7 @@ struct AnsatzArgs {
   double* snap_amps;
   long long* snap_n;
   int64_t snap_stride;
-  long long* stats;  // optional: [0] gates, [1] select passes, [6] max |Phi|
+  long long* stats;  // optional: [0] gates, [1] select passes, [6] max |Phi|, [7] sum of input sizes
 };
 
 int ansatz_blocks_per_sm();

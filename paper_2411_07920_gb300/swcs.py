@@ -53,6 +53,8 @@ _SIGS = {
     "swcs_get_state": ([_vp, _vp, _vp, _i64, _p64], _i),
     "swcs_set_state": ([_vp, _vp, _vp, _i64], _i),
     "swcs_stats": ([_vp, _vp], _i),
+    "swcs_profile_enable": ([_vp, _i], _i),
+    "swcs_profile_read": ([_vp, _vp, _vp, _i], _i),
 }
 
 for _name, (_args, _res) in _SIGS.items():
@@ -208,6 +210,17 @@ class Context:
     def stats(self):
         out = np.zeros(8, np.int64)
         self._ck(lib.swcs_stats(self._h, _ptr(out)))
-        keys = ["gate_passes", "select_passes", "ext_distinct", "ext_buckets", "ext_capacity",
-                "kernel_launches", "n_det_max", "reserved"]
+        keys = ["gates", "select_passes", "ext_distinct", "ext_buckets", "ext_capacity",
+                "kernel_launches", "phi_max", "gate_dets"]
         return dict(zip(keys, out.tolist()))
+
+    KINDS = ("ansatz", "energy", "sigma_scatter", "pool_gather", "table_clear", "other")
+
+    def profile_enable(self, on=True):
+        self._ck(lib.swcs_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self, reset=True):
+        ms = np.zeros(8)
+        n = np.zeros(8, np.int64)
+        self._ck(lib.swcs_profile_read(self._h, _ptr(ms), _ptr(n), 1 if reset else 0))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.KINDS)}
