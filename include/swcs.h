@@ -132,6 +132,29 @@ int swcs_set_state(swcs_ctx* ctx, const uint64_t* h_keys, const double* h_amps, 
  * (gate x determinant applications)}. */
 int swcs_stats(swcs_ctx* ctx, int64_t* h_out8);
 
+/* Largest state accepted by swcs_energy_noalloc. */
+#define SWCS_NOALLOC_MAX_DETS 65536
+
+/* Energy of a state held in the caller's own device buffers, for callers
+ * that must not allocate device memory on their hot path (frameworks that
+ * reserve all device memory in their own allocator, so cudaMalloc fails or
+ * fragments their pool; latency-critical loops where cudaFree would
+ * synchronise the device).  The paper has no counterpart: this is a service
+ * of the library, same quantity as swcs_energy.
+ *   d_keys, d_amps  [n] device arrays: distinct determinants of the loaded
+ *                   Hamiltonian's sector and their amplitudes (no zeros needed)
+ *   n               1 <= n <= SWCS_NOALLOC_MAX_DETS, else SWCS_ERR_INVALID_ARG
+ *   d_out           [2] device: E and <psi|psi>
+ * Needs a loaded Hamiltonian (swcs_load_hamiltonian allocates; this call
+ * does not: no cudaMalloc, cudaFree or allocating library routine).  Its
+ * scratch (index table and accumulators, about 2 MiB) is one static device
+ * array per GPU, held from library load until process exit and cleared by
+ * every call.  The first call on each device looks up that array's device
+ * address; make that first call before any stream capture.  Work is only
+ * enqueued on the context's stream; calls that overlap on the GPU share the
+ * array and race. */
+int swcs_energy_noalloc(swcs_ctx* ctx, const uint64_t* d_keys, const double* d_amps, int64_t n, double* d_out);
+
 /* Per-kernel device time with CUDA events recorded on the context's stream
  * around each launch (off by default).  Kinds: 0 gate/select kernel,
  * 1 energy, 2 sigma scatter, 3 pool gather, 4 table clear, 5 other.

@@ -495,6 +495,23 @@ int sweep(swcs_ctx* c, double* d_g) {
 
 }  // namespace
 
+namespace swcs {
+
+// Used by swcs_energy_noalloc (its own translation unit): the loaded
+// Hamiltonian, the context's stream and the energy kernel's grid size.
+int ctx_ham_for_noalloc(swcs_ctx* c, HamDev* H, cudaStream_t* st, int* nblocks) {
+  const int r = need_ham(c);
+  if (r) return r;
+  *H = ham_dev(c);
+  *st = c->st;
+  *nblocks = c->nsm * sigma_blocks_per_sm();
+  return SWCS_OK;
+}
+
+int ctx_fail_for_noalloc(swcs_ctx* c, int code, const char* msg) { return fail(c, code, "%s", msg); }
+
+}  // namespace swcs
+
 // =============================================================================
 extern "C" {
 

@@ -55,6 +55,7 @@ _SIGS = {
     "swcs_stats": ([_vp, _vp], _i),
     "swcs_profile_enable": ([_vp, _i], _i),
     "swcs_profile_read": ([_vp, _vp, _vp, _i], _i),
+    "swcs_energy_noalloc": ([_vp, _vp, _vp, _i64, _vp], _i),
 }
 
 for _name, (_args, _res) in _SIGS.items():
@@ -206,6 +207,10 @@ class Context:
         keys = _c(keys, np.uint64)
         amps = _c(amps, np.float64)
         self._ck(lib.swcs_set_state(self._h, _ptr(keys), _ptr(amps), len(keys)))
+
+    def energy_noalloc(self, d_keys, d_amps, d_out):
+        """Energy of a state in caller-owned device tensors (no device allocation)."""
+        self._ck(lib.swcs_energy_noalloc(self._h, _tptr(d_keys), _tptr(d_amps), int(d_keys.numel()), _tptr(d_out)))
 
     def stats(self):
         out = np.zeros(8, np.int64)
