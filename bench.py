@@ -3,8 +3,11 @@
 
 One step = one pass of the whole hot path on one synthetic workload:
   apply the 200-gate ansatz from the reference determinant with top-1e6
-  truncation after every gate, the energy, and the full operator-pool
-  gradient (301,600 generalized singles and doubles).
+  truncation after every gate, then one pool sweep, which builds sigma = H psi
+  on the state and its connected space and returns the full operator-pool
+  gradient (301,600 generalized singles and doubles) and the energy.
+The standalone energy kernel (sigma restricted to the state, used for
+energy-only evaluations) is timed separately and reported as `energy_ms`.
 `value` is steps (= pool-gradient sweeps) per second with inputs resident in
 HBM; `e2e` is the same through the host-buffer C-ABI calls, host<->device
 copies included.  `--impl reference` times the CPU oracle on a bounded
@@ -44,6 +47,10 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=400, help="determinants in the oracle's bounded sample")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--sweep", type=int, default=0, help="0 auto, 1 hashed external table, 2 alpha-string rows")
+    p.add_argument("--cluster", type=int, default=2, help="CTAs per alpha-string row cluster")
+    p.add_argument("--rows-l2", type=int, default=0, help="1: cap concurrent rows to about half of L2")
+    p.add_argument("--threads", type=int, default=512, help="threads per CTA of the row sweep")
     return p.parse_args()
 
 
@@ -170,6 +177,10 @@ def run_swcs(args):
     w = I.workload(WORKLOAD, n_keep=args.n_keep)
     ctx = swcs.Context()
     ctx.load_hamiltonian(w.h, w.g, w.n_so, w.n_e)
+    ctx.set_option("sweep", args.sweep)
+    ctx.set_option("cluster", args.cluster)
+    ctx.set_option("rows_l2", args.rows_l2)
+    ctx.set_option("threads", args.threads)
     pool = ctx.pool_size()
     dev = torch.device("cuda", local)
     d_ops = torch.from_numpy(w.ops.reshape(-1).copy()).to(dev)
@@ -181,7 +192,6 @@ def run_swcs(args):
 
     def step():
         ctx.apply_ansatz_dev(d_ops, d_theta, args.n_keep)
-        ctx.energy_dev(d_e)
         ctx.pool_gradients_dev(d_g)
 
     for _ in range(max(args.warmup, 3)):
@@ -210,6 +220,18 @@ def run_swcs(args):
     clk = clocks.stop()
     stats = ctx.stats()
     prof = ctx.profile_read(reset=True)
+    # standalone energy kernel (sigma restricted to the state), timed apart from the step
+    energy_ms = []
+    for _ in range(3):
+        flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        ctx.energy_dev(d_e)
+        ev1.record(stream)
+        ev1.synchronize()
+        energy_ms.append(ev0.elapsed_time(ev1))
+    ctx.profile_read(reset=True)
     ctx.profile_enable(False)
     if world > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
@@ -228,14 +250,19 @@ def run_swcs(args):
     dom_ms, dom_n = kinds[dom]
     buckets = max(stats["ext_buckets"], 1)
     pairs = n_det * (n_conn + 1)
-    per_pair = {"sigma_scatter": 24.0, "pool_gather": 16.0}
+    # algorithmic bytes per connected (D, E) pair: the scatter reads the key and
+    # sigma_E and writes sigma_E (24 B), the gather reads them (16 B); the row
+    # sweep does both in one launch
+    per_pair = {"sigma_scatter": 24.0, "pool_gather": 16.0, "row_sweep": 40.0}
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    if dom in per_pair:
+    if dom == "row_sweep":
+        bytes_per_launch = per_pair[dom] * pairs
+    elif dom in per_pair:
         bytes_per_launch = per_pair[dom] * pairs / buckets
     elif dom == "ansatz":
         # per gate: read S (16 B/det), write and re-read Phi (32 B), select reads (8 B/pass), write S (16 B)
@@ -249,7 +276,7 @@ def run_swcs(args):
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     gate_ms = prof.get("ansatz", (0.0, 0))[0]
     gate_dets_per_s = stats["gate_dets"] / (gate_ms / 1e3) if gate_ms > 0 else None
-    launches = int(sum(v[1] for v in prof.values()))
+    launches = int(stats["kernel_launches"])
 
     # ------------------------------------------------------------ end to end through the host API
     e2e = None
@@ -266,8 +293,8 @@ def run_swcs(args):
             t0 = time.perf_counter()
             ctx.load_hamiltonian(h_np, g_np, w.n_so, w.n_e)
             ctx.apply_ansatz(ops_np, th_np, args.n_keep)
-            e_val, _ = ctx.energy()
             g_host = ctx.pool_gradients()
+            e_val, _ = ctx.sweep_energy()
             dt = time.perf_counter() - t0
             if it > 0:
                 t_e2e += dt
@@ -293,7 +320,7 @@ def run_swcs(args):
                                        f"N={args.n_keep}, GSD pool {pool}",
                            "parallelism": f"replicas x{world}", "l2": "flushed between steps (512 MB write)"},
                 "gate_dets_per_s": gate_dets_per_s, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clk,
+                "gpu_launches": launches, "clocks": clk, "energy_ms": round(min(energy_ms), 3),
                 "kernels_ms": {k: round(v[0], 3) for k, v in prof.items()},
                 "ext": {"distinct": stats["ext_distinct"], "buckets": stats["ext_buckets"],
                         "capacity": stats["ext_capacity"]}}

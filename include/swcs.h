@@ -110,6 +110,10 @@ int swcs_energy_dev(swcs_ctx* ctx, double* d_out);
  * those operators' sigma contributions are formed. */
 int swcs_pool_gradients(swcs_ctx* ctx, double* h_g_out, const int64_t* h_subset, int64_t n_subset);
 int swcs_pool_gradients_dev(swcs_ctx* ctx, double* d_g_out, const int64_t* d_subset, int64_t n_subset);
+/* The pool sweep forms sigma on every determinant of the state as well, so it
+ * also yields E = <psi|H|psi>/<psi|psi>: returns that value from the last
+ * swcs_pool_gradients* call (synchronises). */
+int swcs_sweep_energy(swcs_ctx* ctx, double* h_e_out, double* h_norm2_out);
 
 /* Energy and dE/dtheta of the truncated ansatz, each truncation held as a
  * fixed projector onto its kept set (Sec. II.B, "analytic gradients").
@@ -131,6 +135,16 @@ int swcs_set_state(swcs_ctx* ctx, const uint64_t* h_keys, const double* h_amps, 
  * largest merged set |Phi|, sum over gates of the input state size
  * (gate x determinant applications)}. */
 int swcs_stats(swcs_ctx* ctx, int64_t* h_out8);
+
+/* Tuning options (no effect on results beyond FP64 summation order):
+ *   "sweep"    0 automatic (default), 1 hashed external-sigma table,
+ *              2 alpha-string rows (SWCS_ERR_INVALID_ARG when the sector's
+ *              beta-string space exceeds 2^22 or clusters cannot launch)
+ *   "cluster"  CTAs per alpha-string row in the row sweep, 1..16 (default 2)
+ *   "threads"  threads per CTA of the row sweep: 128, 256 or 512 (default 512)
+ *   "rows_l2"  1: cap the row sweep's concurrent rows to about half of L2;
+ *              0 (default): as many rows as clusters fit on the device */
+int swcs_set_option(swcs_ctx* ctx, const char* name, int64_t value);
 
 /* Largest state accepted by swcs_energy_noalloc. */
 #define SWCS_NOALLOC_MAX_DETS 65536
@@ -157,7 +171,8 @@ int swcs_energy_noalloc(swcs_ctx* ctx, const uint64_t* d_keys, const double* d_a
 
 /* Per-kernel device time with CUDA events recorded on the context's stream
  * around each launch (off by default).  Kinds: 0 gate/select kernel,
- * 1 energy, 2 sigma scatter, 3 pool gather, 4 table clear, 5 other.
+ * 1 energy, 2 hashed sigma scatter, 3 hashed pool gather, 4 table clear,
+ * 5 other, 6 alpha-string row sweep, 7 grouping of the state by alpha string.
  * swcs_profile_read synchronises, returns accumulated milliseconds and launch
  * counts per kind (8 entries each; NULL to skip) and, when reset != 0,
  * clears them together with the swcs_stats counters. */

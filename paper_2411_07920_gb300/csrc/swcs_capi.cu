@@ -53,6 +53,15 @@ struct swcs_ctx {
   DevBuf ops_dev, cs_dev;
   DevBuf gdev, subset_dev, gsub;
 
+  // row sweep: alpha strings of the sector, beta-rank tables, grouped state, rows
+  DevBuf alpha_list, rank_tab, atab, gid_of, gcount, goff, gfill, gkey, gamp, grank, rows;
+  int NA = 0;
+  int64_t NB = 0;
+  int opt_sweep = 0;    // 0 auto, 1 hashed external table, 2 alpha-string rows
+  int opt_cluster = 2;  // CTAs per row cluster
+  int opt_rows_l2 = 0;  // cap concurrent rows to about half of L2
+  int opt_threads = 512;  // threads per CTA of the row sweep
+
   // external sigma table
   DevBuf ext;
   uint64_t ext_cap = 0;
@@ -149,7 +158,7 @@ int ensure_pinned(swcs_ctx* c, size_t bytes) {
 Ctrl* ctrl(swcs_ctx* c) { return (Ctrl*)c->ctrl.p; }
 
 // Kernel kinds for swcs_profile_read.
-enum Kind { kKAnsatz = 0, kKEnergy = 1, kKScatter = 2, kKGather = 3, kKClear = 4, kKOther = 5 };
+enum Kind { kKAnsatz = 0, kKEnergy = 1, kKScatter = 2, kKGather = 3, kKClear = 4, kKOther = 5, kKRow = 6, kKGroup = 7 };
 
 cudaEvent_t take_event(swcs_ctx* c) {
   if (!c->ev_free.empty()) {
@@ -417,7 +426,105 @@ __global__ void sincos_kernel(const double* th, double* cs, int n) {
   }
 }
 
+// Alpha-string row sweep; returns 1 when not applicable (caller falls back).
+int sweep_rows(swcs_ctx* c, double* d_g) {
+  const int m = c->n / 2;
+  if (m > 32 || c->NB <= 0 || c->NB > (1 << 22)) return 1;
+  const int64_t nd = host_state_size(c);
+  if (nd < 0) return fail(c, SWCS_ERR_CUDA, "cannot read state size");
+  Ctrl* k = ctrl(c);
+  const int gsz = std::max(1, std::min(16, c->opt_cluster));
+  const int ks = c->no, nvs = c->nv;
+  const int ns = ks * nvs, ndb = (ks * (ks - 1) / 2) * (nvs * (nvs - 1) / 2);
+  const int max_s = (ns + gsz - 1) / gsz + 1, max_d = (ndb + gsz - 1) / gsz + 1;
+  const int t_same = 1 + ns + ndb;
+  int twords = (int)((c->NB + 31) / 32);
+  size_t smem = row_sweep_smem(max_s, max_d, t_same, twords);
+  if (smem > 96 * 1024) {  // no room for the touched bitmap: clear whole rows
+    twords = 0;
+    smem = row_sweep_smem(max_s, max_d, t_same, 0);
+  }
+  if (smem > 96 * 1024) return 1;
+  int ncl = 0;
+  const int nthr = c->opt_threads;
+  if (row_sweep_max_clusters(nthr, gsz, smem, &ncl) != cudaSuccess || ncl <= 0) {
+    cudaGetLastError();
+    return 1;
+  }
+  // keep the rows of all clusters within about half of L2
+  int l2 = 0;
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->dev);
+  const int64_t row_bytes = c->NB * 8;
+  const int l2_rows = (int)std::max<int64_t>(1, (int64_t)l2 / 2 / std::max<int64_t>(row_bytes, 1));
+  if (c->opt_rows_l2 && ncl > l2_rows) ncl = l2_rows;
+  int r;
+  const uint64_t acap = pow2_at_least((uint64_t)std::max<int64_t>(2 * nd, 64));
+  if ((r = ensure(c, c->atab, acap * sizeof(IdxSlot))) || (r = ensure(c, c->gid_of, nd * 4 + 4)) ||
+      (r = ensure(c, c->gcount, nd * 8 + 8)) || (r = ensure(c, c->goff, nd * 8 + 16)) ||
+      (r = ensure(c, c->gfill, nd * 8 + 8)) || (r = ensure(c, c->gkey, nd * 8 + 8)) ||
+      (r = ensure(c, c->gamp, nd * 8 + 8)) || (r = ensure(c, c->grank, nd * 4 + 4)) ||
+      (r = ensure(c, c->rows, (size_t)ncl * c->NB * 8)))
+    return r;
+  CK(cudaMemsetAsync(c->atab.p, 0xff, acap * sizeof(IdxSlot), c->st));
+  CK(cudaMemsetAsync(c->gcount.p, 0, nd * 8 + 8, c->st));
+  CK(cudaMemsetAsync(c->gfill.p, 0, nd * 8 + 8, c->st));
+  CK(cudaMemsetAsync(&k->n_distinct, 0, 8, c->st));
+  CK(cudaMemsetAsync(k->acc, 0, 16, c->st));
+  CK(cudaMemsetAsync(d_g, 0, sizeof(double) * c->pool_size, c->st));
+  CK(cudaMemsetAsync(c->rows.p, 0, (size_t)ncl * c->NB * 8, c->st));
+  GroupArgs ga;
+  ga.keys = (const uint64_t*)c->keys_a.p;
+  ga.amps = (const double*)c->amps_a.p;
+  ga.n = &k->n_state;
+  ga.atab = (IdxSlot*)c->atab.p;
+  ga.amask = acap - 1;
+  ga.n_groups = &k->n_distinct;
+  ga.gid_of = (uint32_t*)c->gid_of.p;
+  ga.gcount = (long long*)c->gcount.p;
+  ga.goff = (long long*)c->goff.p;
+  ga.gfill = (long long*)c->gfill.p;
+  ga.gkey = (uint64_t*)c->gkey.p;
+  ga.gamp = (double*)c->gamp.p;
+  ga.grank = (uint32_t*)c->grank.p;
+  ga.rank_tab = (const uint32_t*)c->rank_tab.p;
+  ga.ks = ks;
+  ga.acc = k->acc;
+  CK(launch_k(c, kKGroup, [&] { return launch_group_state(ga, c->st); }));
+  c->launches += 4;  // five grouping kernels in one call
+  RowArgs ra;
+  ra.H = ham_dev(c);
+  ra.gkey = ga.gkey;
+  ra.gamp = ga.gamp;
+  ra.grank = ga.grank;
+  ra.goff = ga.goff;
+  ra.atab = ga.atab;
+  ra.amask = ga.amask;
+  ra.alpha_list = (const uint32_t*)c->alpha_list.p;
+  ra.NA = c->NA;
+  ra.rank_tab = ga.rank_tab;
+  ra.rows = (double*)c->rows.p;
+  ra.NB = c->NB;
+  ra.g = d_g;
+  ra.acc = k->acc;
+  ra.err = &k->err;
+  ra.max_ent_s = max_s;
+  ra.max_ent_d = max_d;
+  ra.touched_words = twords;
+  CK(launch_k(c, kKRow, [&] { return launch_row_sweep(ra, nthr, gsz, ncl, smem, c->st); }));
+  c->stats[2] = 0;
+  c->stats[3] = ncl;
+  c->stats[4] = (int64_t)ncl * c->NB;
+  CK(launch_k(c, kKOther, [&] { return launch_scale_gradient(d_g, c->pool_size, k->acc, c->st); }));
+  CK(launch_k(c, kKOther, [&] { return launch_finalize_energy(k->acc, k->eout, c->st); }));
+  return SWCS_OK;
+}
+
 int sweep(swcs_ctx* c, double* d_g) {
+  if (c->opt_sweep != 1) {
+    const int r = sweep_rows(c, d_g);
+    if (r != 1) return r;
+    if (c->opt_sweep == 2) return fail(c, SWCS_ERR_INVALID_ARG, "row sweep not applicable to this sector");
+  }
   const HamDev H = ham_dev(c);
   const StateDev S = state_dev(c);
   Ctrl* k = ctrl(c);
@@ -540,7 +647,8 @@ int swcs_destroy(swcs_ctx* c) {
   cudaStreamSynchronize(c->st);
   DevBuf* bufs[] = {&c->h, &c->J, &c->Ws, &c->G, &c->opd, &c->ops1, &c->gstage, &c->keys_a, &c->amps_a,
                     &c->keys_b, &c->amps_b, &c->tab0, &c->tab1, &c->ctrl, &c->ops_dev, &c->cs_dev,
-                    &c->gdev, &c->subset_dev, &c->gsub, &c->ext};
+                    &c->gdev, &c->subset_dev, &c->gsub, &c->ext, &c->alpha_list, &c->rank_tab, &c->atab,
+                    &c->gid_of, &c->gcount, &c->goff, &c->gfill, &c->gkey, &c->gamp, &c->grank, &c->rows};
   for (DevBuf* b : bufs) release(*b);
   if (c->pin) cudaFreeHost(c->pin);
   for (auto& e : c->ev_pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
@@ -578,6 +686,40 @@ int swcs_load_hamiltonian(swcs_ctx* c, const double* h_h, const double* h_g, int
   CK(launch_k(c, kKOther, [&] { return launch_pack_hamiltonian((const double*)c->gstage.p, n, (double*)c->J.p, (double*)c->Ws.p, (double*)c->G.p, c->st); }));
   std::vector<int> opd, ops1;
   build_pool(c, opd, ops1);
+  {
+    // alpha strings of the sector and per-byte colex rank tables of one spin
+    const int m = n / 2, ks = c->no;
+    std::vector<uint32_t> al;
+    if (m <= 32) {
+      uint64_t v = (1ull << ks) - 1ull;
+      while (v < (1ull << m)) {
+        al.push_back((uint32_t)v);
+        const uint64_t t = v | (v - 1);
+        v = (t + 1) | (((~t & -~t) - 1) >> (__builtin_ctzll(v) + 1));
+      }
+    }
+    c->NA = (int)al.size();
+    c->NB = (int64_t)al.size();
+    std::vector<uint32_t> T((size_t)4 * (ks + 1) * 256, 0u);
+    for (int ch = 0; ch < 4; ++ch)
+      for (int j = 0; j <= ks; ++j)
+        for (int byte = 0; byte < 256; ++byte) {
+          int i = j;
+          double r = 0.0;
+          bool ok = true;
+          for (int b = 0; b < 8; ++b)
+            if ((byte >> b) & 1) {
+              const int pos = 8 * ch + b;
+              if (pos >= m || i >= ks) { ok = false; break; }
+              r += binom(pos, i + 1);
+              ++i;
+            }
+          T[((size_t)ch * (ks + 1) + j) * 256 + byte] = ok ? (uint32_t)r : 0u;
+        }
+    if ((r = ensure(c, c->alpha_list, al.size() * 4 + 4)) || (r = ensure(c, c->rank_tab, T.size() * 4))) return r;
+    if (!al.empty()) CK(cudaMemcpyAsync(c->alpha_list.p, al.data(), al.size() * 4, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->rank_tab.p, T.data(), T.size() * 4, cudaMemcpyHostToDevice, c->st));
+  }
   CK(cudaMemcpyAsync(c->opd.p, opd.data(), np2 * 4, cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(c->ops1.p, ops1.data(), n2 * 4, cudaMemcpyHostToDevice, c->st));
   CK(cudaStreamSynchronize(c->st));
@@ -803,6 +945,37 @@ int swcs_stats(swcs_ctx* c, int64_t* out8) {
   out8[5] = c->launches;
   out8[6] = dev[6];
   out8[7] = dev[7];
+  return SWCS_OK;
+}
+
+int swcs_sweep_energy(swcs_ctx* c, double* e_out, double* n2_out) {
+  int r = need_state(c);
+  if (r) return r;
+  double out[2];
+  CK(cudaMemcpyAsync(out, ctrl(c)->eout, 16, cudaMemcpyDeviceToHost, c->st));
+  if ((r = check_device(c, "swcs_sweep_energy"))) return r;
+  if (e_out) *e_out = out[0];
+  if (n2_out) *n2_out = out[1];
+  return SWCS_OK;
+}
+
+int swcs_set_option(swcs_ctx* c, const char* name, int64_t value) {
+  if (!c || !name) return SWCS_ERR_INVALID_ARG;
+  const std::string k(name);
+  if (k == "sweep") {
+    if (value < 0 || value > 2) return fail(c, SWCS_ERR_INVALID_ARG, "sweep must be 0, 1 or 2");
+    c->opt_sweep = (int)value;
+  } else if (k == "threads") {
+    if (value != 128 && value != 256 && value != 512) return fail(c, SWCS_ERR_INVALID_ARG, "threads must be 128, 256 or 512");
+    c->opt_threads = (int)value;
+  } else if (k == "rows_l2") {
+    c->opt_rows_l2 = value != 0;
+  } else if (k == "cluster") {
+    if (value < 1 || value > 16) return fail(c, SWCS_ERR_INVALID_ARG, "cluster must be 1..16");
+    c->opt_cluster = (int)value;
+  } else {
+    return fail(c, SWCS_ERR_INVALID_ARG, "unknown option '%s'", name);
+  }
   return SWCS_OK;
 }
 

@@ -96,6 +96,51 @@ cudaError_t launch_scale_gradient(double* g, int64_t n, const double* acc, cudaS
 cudaError_t launch_gather_subset(const double* g, const int64_t* subset, int64_t n, double* out, cudaStream_t st);
 int sigma_blocks_per_sm();
 
+// Row sweep (alpha-string rows): see swcs_rowsweep.cu.
+struct RowArgs {
+  HamDev H;
+  const uint64_t* gkey;   // state grouped by alpha string
+  const double* gamp;
+  const uint32_t* grank;  // rank of each determinant's beta string
+  const long long* goff;  // [G+1] group offsets
+  const IdxSlot* atab;    // alpha string -> group id
+  uint64_t amask;
+  const uint32_t* alpha_list;  // every alpha string of the sector
+  int NA;
+  const uint32_t* rank_tab;    // [4][ks+1][256]
+  double* rows;                // [clusters][NB]
+  int64_t NB;
+  double* g;
+  double* acc;                 // acc[0] += sum c_D sigma_D
+  int* err;
+  int max_ent_s, max_ent_d;
+  int touched_words;  // words of the per-CTA touched-entry bitmap (0: clear whole rows)
+};
+
+struct GroupArgs {
+  const uint64_t* keys;
+  const double* amps;
+  const long long* n;
+  IdxSlot* atab;
+  uint64_t amask;
+  unsigned long long* n_groups;
+  uint32_t* gid_of;
+  long long* gcount;
+  long long* goff;
+  long long* gfill;
+  uint64_t* gkey;
+  double* gamp;
+  uint32_t* grank;
+  const uint32_t* rank_tab;
+  int ks;
+  double* acc;  // acc[1] += sum c^2
+};
+
+size_t row_sweep_smem(int max_ent_s, int max_ent_d, int t_same, int touched_words);
+cudaError_t row_sweep_max_clusters(int threads, int gsz, size_t smem, int* n_clusters);
+cudaError_t launch_row_sweep(const RowArgs& a, int threads, int gsz, int n_clusters, size_t smem, cudaStream_t st);
+cudaError_t launch_group_state(const GroupArgs& g, cudaStream_t st);
+
 // Hamiltonian preparation from the full <pq||rs> array on the device.
 cudaError_t launch_pack_hamiltonian(const double* g_full, int n, double* J, double* Ws, double* G,
                                     cudaStream_t st);

@@ -1,0 +1,576 @@
+// Pool-gradient sweep organised by alpha strings ("row sweep").
+//
+// The quantity is the same as the hashed sweep (ADAPT step 4, Sec. II.C):
+//   sigma_E = sum_{D in S} <E|H|D> c_D   for every E connected to S,
+//   g_k     = (2/<psi|psi>) sum_{(D,E)} dir * phase * c_D * sigma_E,
+// but the external space is walked one target alpha string X at a time.
+// Every determinant is a pair (alpha string, beta string); a connected pair
+// (D, E) with E_alpha = X has D_alpha = X (beta-side excitation or the
+// diagonal), D_alpha one alpha single away from X (alpha single or
+// alpha-beta double) or one alpha double away (alpha-alpha double).  For a
+// fixed X all sigma_E therefore live in one dense row indexed by the
+// combinatorial rank of E_beta (C(n/2, n_e/2) doubles, 1.84 MB at 52/12),
+// which a thread-block cluster keeps in L2:
+//   1. the cluster finds the alpha groups of S at distance 0, 1, 2 from X
+//      (alpha-string hash table of S);
+//   2. scatter: every pair adds <E|H|D> c_D into row[rank(E_beta)];
+//   3. cluster barrier; gather: every pair adds dir*phase*c_D*row[...] to
+//      g_k, and the diagonal pairs give the energy numerator;
+//   4. cluster barrier; the cluster clears the row; barrier; next X.
+// No hashing or compare-and-swap on sigma, and no sigma traffic to HBM.
+#include <cooperative_groups.h>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "swcs_device.cuh"
+#include "swcs_kernels.h"
+
+namespace cg = cooperative_groups;
+
+namespace swcs {
+
+namespace {
+
+constexpr int kRowMaxWarps = 16;  // CTA sizes 128, 256 or 512 threads
+constexpr int kSameChunk = 128;  // targets of one determinant per work item (4 per lane)
+constexpr int kDblChunk = 1;     // determinants per alpha-double work item
+
+__device__ __forceinline__ uint32_t even_bits(uint64_t x) {
+  x &= 0x5555555555555555ull;
+  x = (x | (x >> 1)) & 0x3333333333333333ull;
+  x = (x | (x >> 2)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x | (x >> 4)) & 0x00FF00FF00FF00FFull;
+  x = (x | (x >> 8)) & 0x0000FFFF0000FFFFull;
+  x = (x | (x >> 16)) & 0x00000000FFFFFFFFull;
+  return (uint32_t)x;
+}
+
+// Colex rank of a string of one spin: sum_i C(p_i, i+1) over its set bits,
+// from per-byte tables T[chunk][bits below chunk][byte].
+__device__ __forceinline__ uint32_t str_rank(const uint32_t* __restrict__ T, int ks, uint32_t m) {
+  uint32_t r = 0;
+  int below = 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const uint32_t byte = (m >> (8 * c)) & 255u;
+    if (byte) r += __ldg(&T[(c * (ks + 1) + below) * 256 + byte]);
+    below += __popc(byte);
+  }
+  return r;
+}
+
+struct RowEnt {
+  uint32_t gid;
+  uint32_t flat;  // exclusive prefix of work items within its list
+  uint8_t o[4];   // spin-orbitals removed from D (o[0], o[1]) and added (o[2], o[3]); singles use o[0], o[2]
+};
+
+struct RowShared {
+  uint16_t tri_o[kMaxSpin * (kMaxSpin - 1) / 2];
+  uint16_t tri_v[kMaxSpin * (kMaxSpin - 1) / 2];
+  uint8_t occx[kMaxSpin], virx[kMaxSpin];
+  uint8_t bocc[kRowMaxWarps][kMaxSpin], bvir[kRowMaxWarps][kMaxSpin];  // beta spatial lists per warp
+  uint8_t occ_all[kRowMaxWarps][64];
+  int n_s, n_d;              // entries found
+  uint32_t tot_s, tot_d;     // work items (singles: entry x determinant; doubles: entry x chunk)
+  long long gx_off, gx_cnt;  // the alpha group of X itself
+  unsigned scan_tmp[kRowMaxWarps];
+  double red[kRowMaxWarps];
+};
+
+// Dynamic shared memory: entry lists, the decode table of X's own targets and
+// the bitmap of row entries this CTA touched.
+struct RowDyn {
+  RowEnt* ents_s;
+  RowEnt* ents_d;
+  uint32_t* same_tab;  // target t >= 1 of a determinant in X's group: o1 | o2<<8 | v1<<16 | v2<<24 (o2 = 255: single)
+  unsigned* touched;   // NB bits (nullptr: clear whole rows)
+};
+
+__device__ __forceinline__ double fock_single(const RowArgs& A, const uint8_t* occ_all, int p, int q) {
+  const int n = A.H.n;
+  double f = A.H.h[q * n + p];
+  const double* w = A.H.Ws + ((size_t)p * n + q) * n;
+  for (int t = 0; t < A.H.ne; ++t) f += w[occ_all[t]];
+  return f;
+}
+
+__device__ __forceinline__ void mark(unsigned* touched, uint32_t i) {
+  if (touched) atomicOr(&touched[i >> 5], 1u << (i & 31));
+}
+
+// One connected pair, scatter or gather.  (p<q) removed, (r<s) added for
+// doubles; q = s = -1 marks a single p -> r.
+template <bool SCATTER>
+__device__ __forceinline__ void row_pair(const RowArgs& A, double* row, unsigned* touched, uint64_t d, double cd,
+                                         uint32_t rank_e, int p, int q, int r, int s, const uint8_t* occ_all) {
+  const int n = A.H.n;
+  if (q < 0) {
+    const int sb = single_phase(d, p, r);
+    if (SCATTER) {
+      atomicAdd(&row[rank_e], apply_sign(fock_single(A, occ_all, p, r), sb) * cd);
+      mark(touched, rank_e);
+    } else {
+      const int lo = p < r ? p : r, hi = p < r ? r : p;
+      const int k = A.H.ops1[lo * n + hi];
+      atomicAdd(&A.g[k], apply_sign(cd * row[rank_e], sb ^ (int)(p > r)));
+    }
+    return;
+  }
+  const int sb = double_phase(d, p, q, r, s);
+  const int pa = pair_index(p, q, n), pb = pair_index(r, s, n);
+  if (SCATTER) {
+    atomicAdd(&row[rank_e], apply_sign(A.H.G[(size_t)pa * A.H.npairs + pb], sb) * cd);
+    mark(touched, rank_e);
+  } else {
+    const bool down = pa > pb;
+    const int k = down ? A.H.opd[(size_t)pb * A.H.npairs + pa] : A.H.opd[(size_t)pa * A.H.npairs + pb];
+    atomicAdd(&A.g[k], apply_sign(cd * row[rank_e], sb ^ (int)down));
+  }
+}
+
+__device__ __forceinline__ void warp_lists(RowShared& sh, int warp, int lane, uint64_t d, int m) {
+  const bool inr = lane < m;
+  const bool ob = inr && ((d >> (2 * lane + 1)) & 1ull);
+  const unsigned bo = __ballot_sync(0xffffffffu, ob);
+  const unsigned bv = __ballot_sync(0xffffffffu, inr && !ob);
+  const unsigned below = (1u << lane) - 1u;
+  if (ob) sh.bocc[warp][__popc(bo & below)] = (uint8_t)lane;
+  else if (inr) sh.bvir[warp][__popc(bv & below)] = (uint8_t)lane;
+  const unsigned lo = (unsigned)d, hi = (unsigned)(d >> 32);
+  if ((lo >> lane) & 1u) sh.occ_all[warp][__popc(lo & below)] = (uint8_t)lane;
+  if ((hi >> lane) & 1u) sh.occ_all[warp][__popc(lo) + __popc(hi & below)] = (uint8_t)(32 + lane);
+  __syncwarp();
+}
+
+// Block-wide exclusive scan, in list order, of the work items of each entry:
+// ceil(group size / chunk).
+template <int kRowThreads>
+__device__ void scan_items(RowShared& sh, RowEnt* ents, int cnt, const long long* goff, int chunk, uint32_t* total) {
+  const int per = (cnt + kRowThreads - 1) / kRowThreads;
+  const int b = threadIdx.x * per, e = min(cnt, b + per);
+  auto items = [&](int i) {
+    const unsigned sz = (unsigned)(goff[ents[i].gid + 1] - goff[ents[i].gid]);
+    return (sz + chunk - 1) / chunk;
+  };
+  unsigned sum = 0;
+  for (int i = b; i < e; ++i) sum += items(i);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned inc = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  if (lane == 31) sh.scan_tmp[warp] = inc;
+  __syncthreads();
+  unsigned wbase = 0;
+  for (int w = 0; w < warp; ++w) wbase += sh.scan_tmp[w];
+  unsigned run = wbase + inc - sum;
+  for (int i = b; i < e; ++i) {
+    ents[i].flat = run;
+    run += items(i);
+  }
+  if (threadIdx.x == kRowThreads - 1) *total = run;
+  __syncthreads();
+}
+
+__device__ __forceinline__ int find_entry(const RowEnt* ents, int cnt, uint32_t t) {
+  int lo = 0, hi = cnt - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (ents[mid].flat <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int kRowThreads, bool SCATTER>
+__device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, double* row, int crank, int gsz,
+                          double& e_acc) {
+  constexpr int kRowWarps = kRowThreads / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m = A.H.n >> 1, ks = A.H.no, nvs = A.H.nv;
+  const int n_tv = nvs * (nvs - 1) / 2;
+  const int t_same = 1 + ks * nvs + (ks * (ks - 1) / 2) * n_tv;
+  const int nch = (t_same + kSameChunk - 1) / kSameChunk;
+  unsigned* touched = SCATTER ? dy.touched : nullptr;
+  // ---------------- X's own group: diagonal, beta singles, beta-beta doubles; items (determinant, chunk)
+  const long long n_items_same = sh.gx_cnt * nch;
+  for (long long u = (long long)crank * kRowWarps + warp; u < n_items_same; u += (long long)gsz * kRowWarps) {
+    const long long j = u / nch;
+    const int ch = (int)(u - j * nch);
+    const long long di = sh.gx_off + j;
+    const uint64_t d = A.gkey[di];
+    const double cd = A.gamp[di];
+    const uint32_t db = even_bits(d >> 1);
+    warp_lists(sh, warp, lane, d, m);
+    const uint8_t* oa = sh.occ_all[warp];
+    if (ch == 0) {  // diagonal <D|H|D> = sum_i h_ii + 1/2 sum_ij <ij||ij>
+      double hd = 0.0;
+      for (int t2 = lane; t2 < A.H.ne; t2 += 32) {
+        const int a = oa[t2];
+        double jj = 0.0;
+        for (int u2 = 0; u2 < A.H.ne; ++u2) jj += A.H.J[a * A.H.n + oa[u2]];
+        hd += A.H.h[a * A.H.n + a] + 0.5 * jj;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) hd += __shfl_xor_sync(0xffffffffu, hd, o);
+      if (lane == 0) {
+        const uint32_t rd = A.grank[di];
+        if (SCATTER) {
+          atomicAdd(&row[rd], hd * cd);
+          mark(touched, rd);
+        } else {
+          e_acc += cd * row[rd];
+        }
+      }
+    }
+    const int t_end = min(t_same, (ch + 1) * kSameChunk);
+    for (int t = max(1, ch * kSameChunk) + lane; t < t_end; t += 32) {
+      const uint32_t code = dy.same_tab[t];
+      const int o1 = code & 255, o2 = (code >> 8) & 255, v1 = (code >> 16) & 255, v2 = code >> 24;
+      if (o2 == 255) {
+        const int i = sh.bocc[warp][o1], jv = sh.bvir[warp][v1];
+        const uint32_t re = str_rank(A.rank_tab, ks, db ^ (1u << i) ^ (1u << jv));
+        row_pair<SCATTER>(A, row, touched, d, cd, re, 2 * i + 1, -1, 2 * jv + 1, -1, oa);
+      } else {
+        const int i1 = sh.bocc[warp][o1], i2 = sh.bocc[warp][o2];
+        const int j1 = sh.bvir[warp][v1], j2 = sh.bvir[warp][v2];
+        const uint32_t re = str_rank(A.rank_tab, ks, db ^ (1u << i1) ^ (1u << i2) ^ (1u << j1) ^ (1u << j2));
+        row_pair<SCATTER>(A, row, touched, d, cd, re, 2 * i1 + 1, 2 * i2 + 1, 2 * j1 + 1, 2 * j2 + 1, oa);
+      }
+    }
+    __syncwarp();
+  }
+  // ---------------- alpha-single neighbours: alpha single + alpha-beta doubles (warp per determinant)
+  for (uint32_t t = warp; t < sh.tot_s; t += kRowWarps) {
+    const int e = find_entry(dy.ents_s, sh.n_s, t);
+    const RowEnt en = dy.ents_s[e];
+    const long long di = A.goff[en.gid] + (t - en.flat);
+    const uint64_t d = A.gkey[di];
+    const double cd = A.gamp[di];
+    const uint32_t db = even_bits(d >> 1);
+    warp_lists(sh, warp, lane, d, m);
+    const uint8_t* oa = sh.occ_all[warp];
+    const int pa = en.o[0], pb = en.o[2];  // alpha spin-orbitals: removed, added
+    if (lane == 0) row_pair<SCATTER>(A, row, touched, d, cd, A.grank[di], pa, -1, pb, -1, oa);
+    for (int t2 = lane; t2 < ks * nvs; t2 += 32) {
+      const int i = sh.bocc[warp][t2 / nvs], j = sh.bvir[warp][t2 % nvs];
+      const int bi = 2 * i + 1, bj = 2 * j + 1;
+      const uint32_t re = str_rank(A.rank_tab, ks, db ^ (1u << i) ^ (1u << j));
+      row_pair<SCATTER>(A, row, touched, d, cd, re, min(pa, bi), max(pa, bi), min(pb, bj), max(pb, bj), oa);
+    }
+    __syncwarp();
+  }
+  // ---------------- alpha-double neighbours: one determinant per lane; lane 0 of each warp
+  // finds the entry of the warp's first item, the other lanes walk forward from it
+  for (uint32_t t0 = (uint32_t)warp * 32; t0 < sh.tot_d; t0 += kRowThreads) {
+    int e = 0;
+    if (lane == 0) e = find_entry(dy.ents_d, sh.n_d, t0);
+    e = __shfl_sync(0xffffffffu, e, 0);
+    const uint32_t t = t0 + lane;
+    if (t < sh.tot_d) {
+      while (e + 1 < sh.n_d && dy.ents_d[e + 1].flat <= t) ++e;
+      const RowEnt en = dy.ents_d[e];
+      const long long di = A.goff[en.gid] + (t - en.flat);
+      row_pair<SCATTER>(A, row, touched, A.gkey[di], A.gamp[di], A.grank[di], en.o[0], en.o[1], en.o[2], en.o[3],
+                        nullptr);
+    }
+  }
+}
+
+template <int kRowThreads>
+__global__ void __launch_bounds__(kRowThreads)
+row_sweep_kernel(RowArgs A) {
+  constexpr int kRowWarps = kRowThreads / 32;
+  extern __shared__ __align__(16) unsigned char dyn[];
+  __shared__ RowShared sh;
+  cg::cluster_group cl = cg::this_cluster();
+  const int crank = (int)cl.block_rank();
+  const int gsz = (int)cl.num_blocks();
+  const int cid = blockIdx.x / gsz, ncl = gridDim.x / gsz;
+  double* row = A.rows + (size_t)cid * A.NB;
+  const int m = A.H.n >> 1, ks = A.H.no, nvs = A.H.nv;
+  const int n_to = ks * (ks - 1) / 2, n_tv = nvs * (nvs - 1) / 2;
+  const int ns = ks * nvs, nd = n_to * n_tv;
+  const int t_same = 1 + ns + nd;
+  const int nwords = A.touched_words;
+  RowDyn dy;
+  dy.ents_s = (RowEnt*)dyn;
+  dy.ents_d = dy.ents_s + A.max_ent_s;
+  dy.same_tab = (uint32_t*)(dy.ents_d + A.max_ent_d);
+  dy.touched = nwords > 0 ? (unsigned*)(dy.same_tab + t_same) : nullptr;
+
+  for (int t = threadIdx.x; t < n_to || t < n_tv; t += blockDim.x) {
+    auto dec = [](int t, int L) -> uint16_t {
+      int a = 0, base = 0;
+      while (base + (L - 1 - a) <= t) { base += L - 1 - a; ++a; }
+      return (uint16_t)(a | ((a + 1 + (t - base)) << 8));
+    };
+    if (t < n_to) sh.tri_o[t] = dec(t, ks);
+    if (t < n_tv) sh.tri_v[t] = dec(t, nvs);
+  }
+  for (int w = threadIdx.x; w < nwords; w += kRowThreads) dy.touched[w] = 0u;
+  __syncthreads();
+  for (int t = 1 + threadIdx.x; t < t_same; t += kRowThreads) {
+    uint32_t code;
+    if (t - 1 < ns) {
+      code = (uint32_t)((t - 1) / nvs) | (255u << 8) | ((uint32_t)((t - 1) % nvs) << 16);
+    } else {
+      const int dd = t - 1 - ns;
+      const uint16_t oo = sh.tri_o[dd / n_tv], vv = sh.tri_v[dd % n_tv];
+      code = (uint32_t)(oo & 255) | ((uint32_t)(oo >> 8) << 8) | ((uint32_t)(vv & 255) << 16) | ((uint32_t)(vv >> 8) << 24);
+    }
+    dy.same_tab[t] = code;
+  }
+  double e_acc = 0.0;
+  __syncthreads();
+
+  for (int xi = cid; xi < A.NA; xi += ncl) {
+    const uint32_t X = A.alpha_list[xi];
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      const bool inr = lane < m;
+      const bool o = inr && ((X >> lane) & 1u);
+      const unsigned bo = __ballot_sync(0xffffffffu, o), bv = __ballot_sync(0xffffffffu, inr && !o);
+      const unsigned below = (1u << lane) - 1u;
+      if (o) sh.occx[__popc(bo & below)] = (uint8_t)lane;
+      else if (inr) sh.virx[__popc(bv & below)] = (uint8_t)lane;
+      if (lane == 0) {
+        sh.n_s = 0;
+        sh.n_d = 0;
+        const int64_t g = idx_lookup(A.atab, A.amask, (uint64_t)X);
+        sh.gx_off = g >= 0 ? A.goff[g] : 0;
+        sh.gx_cnt = g >= 0 ? A.goff[g + 1] - A.goff[g] : 0;
+      }
+    }
+    __syncthreads();
+    // candidates c = 0 .. ns+nd-1 (alpha singles then doubles of X); this CTA takes c = crank (mod gsz)
+    for (int cc = threadIdx.x; crank + cc * gsz < ns + nd; cc += kRowThreads) {
+      const int c = crank + cc * gsz;
+      uint32_t Y;
+      uint8_t o4[4];
+      const bool single = c < ns;
+      if (single) {
+        const int b = sh.occx[c / nvs], a = sh.virx[c % nvs];
+        Y = X ^ (1u << b) ^ (1u << a);
+        o4[0] = (uint8_t)(2 * a); o4[1] = 0; o4[2] = (uint8_t)(2 * b); o4[3] = 0;
+      } else {
+        const int dd = c - ns;
+        const uint16_t oo = sh.tri_o[dd / n_tv], vv = sh.tri_v[dd % n_tv];
+        const int b1 = sh.occx[oo & 255], b2 = sh.occx[oo >> 8];
+        const int a1 = sh.virx[vv & 255], a2 = sh.virx[vv >> 8];
+        Y = X ^ (1u << b1) ^ (1u << b2) ^ (1u << a1) ^ (1u << a2);
+        o4[0] = (uint8_t)(2 * a1); o4[1] = (uint8_t)(2 * a2); o4[2] = (uint8_t)(2 * b1); o4[3] = (uint8_t)(2 * b2);
+      }
+      const int64_t g = idx_lookup(A.atab, A.amask, (uint64_t)Y);
+      if (g >= 0) {
+        RowEnt en;
+        en.gid = (uint32_t)g;
+        en.flat = 0;
+        en.o[0] = o4[0]; en.o[1] = o4[1]; en.o[2] = o4[2]; en.o[3] = o4[3];
+        if (single) {
+          const int slot = atomicAdd(&sh.n_s, 1);
+          if (slot < A.max_ent_s) dy.ents_s[slot] = en;
+        } else {
+          const int slot = atomicAdd(&sh.n_d, 1);
+          if (slot < A.max_ent_d) dy.ents_d[slot] = en;
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (sh.n_s > A.max_ent_s || sh.n_d > A.max_ent_d) set_error(A.err, kDevBadState);
+      sh.n_s = min(sh.n_s, A.max_ent_s);
+      sh.n_d = min(sh.n_d, A.max_ent_d);
+    }
+    __syncthreads();
+    scan_items<kRowThreads>(sh, dy.ents_s, sh.n_s, A.goff, 1, &sh.tot_s);
+    scan_items<kRowThreads>(sh, dy.ents_d, sh.n_d, A.goff, kDblChunk, &sh.tot_d);
+
+    row_phase<kRowThreads, true>(A, sh, dy, row, crank, gsz, e_acc);
+    cl.sync();
+    row_phase<kRowThreads, false>(A, sh, dy, row, crank, gsz, e_acc);
+    cl.sync();
+    if (dy.touched) {  // clear the entries this CTA touched (others clear theirs)
+      for (int w = threadIdx.x; w < nwords; w += kRowThreads) {
+        unsigned bits = dy.touched[w];
+        if (!bits) continue;
+        dy.touched[w] = 0u;
+        while (bits) {
+          const int b = __ffs(bits) - 1;
+          bits &= bits - 1u;
+          row[(size_t)w * 32 + b] = 0.0;
+        }
+      }
+    } else {  // clear this CTA's slice of the row
+      const int64_t per = (A.NB + gsz - 1) / gsz;
+      const int64_t b = per * crank, e = (A.NB < b + per) ? A.NB : b + per;
+      for (int64_t i = b + threadIdx.x; i < e; i += kRowThreads) row[i] = 0.0;
+    }
+    cl.sync();
+  }
+  // energy numerator
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e_acc += __shfl_xor_sync(0xffffffffu, e_acc, o);
+  if (lane == 0) sh.red[warp] = e_acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kRowWarps; ++w) s += sh.red[w];
+    if (s != 0.0) atomicAdd(&A.acc[0], s);
+  }
+}
+
+// ---------------------------------------------------------------- grouping by alpha string
+__global__ void group_insert_kernel(const uint64_t* keys, const long long* n_ptr, IdxSlot* tab, uint64_t mask,
+                                    const double* amps, double* acc) {
+  const long long n = *n_ptr;
+  double s2 = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const uint64_t a = even_bits(keys[i]);
+    uint64_t s = mix64(a) & mask;
+    for (uint64_t k = 0; k <= mask; ++k) {
+      const unsigned long long prev =
+          atomicCAS((unsigned long long*)&tab[s].key, (unsigned long long)kEmpty, (unsigned long long)a);
+      if (prev == kEmpty || prev == a) break;
+      s = (s + 1) & mask;
+    }
+    s2 += amps[i] * amps[i];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  if ((threadIdx.x & 31) == 0 && s2 != 0.0) atomicAdd(&acc[1], s2);
+}
+
+__global__ void group_ids_kernel(IdxSlot* tab, uint64_t cap, unsigned long long* n_groups) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += (uint64_t)gridDim.x * blockDim.x)
+    if (tab[i].key != kEmpty) tab[i].idx = atomicAdd(n_groups, 1ull);
+}
+
+__global__ void group_count_kernel(const uint64_t* keys, const long long* n_ptr, const IdxSlot* tab, uint64_t mask,
+                                   uint32_t* gid_of, long long* gcount) {
+  const long long n = *n_ptr;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int64_t g = idx_lookup(tab, mask, (uint64_t)even_bits(keys[i]));
+    gid_of[i] = (uint32_t)g;
+    atomicAdd((unsigned long long*)&gcount[g], 1ull);
+  }
+}
+
+// Exclusive scan of gcount[0..G) into goff[0..G] by one block.
+__global__ void group_scan_kernel(const long long* gcount, const unsigned long long* n_groups, long long* goff) {
+  __shared__ long long part[1024];
+  const long long G = (long long)*n_groups;
+  const long long per = (G + blockDim.x - 1) / blockDim.x;
+  const long long b = threadIdx.x * per, e = min(G, b + per);
+  long long s = 0;
+  for (long long i = b; i < e; ++i) s += gcount[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long run = 0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      const long long v = part[t];
+      part[t] = run;
+      run += v;
+    }
+    goff[G] = run;
+  }
+  __syncthreads();
+  long long run = part[threadIdx.x];
+  for (long long i = b; i < e; ++i) {
+    goff[i] = run;
+    run += gcount[i];
+  }
+}
+
+__global__ void group_scatter_kernel(const uint64_t* keys, const double* amps, const long long* n_ptr,
+                                     const uint32_t* gid_of, const long long* goff, long long* gfill,
+                                     uint64_t* gkey, double* gamp, uint32_t* grank, const uint32_t* rank_tab, int ks) {
+  const long long n = *n_ptr;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const uint32_t g = gid_of[i];
+    const long long pos = goff[g] + (long long)atomicAdd((unsigned long long*)&gfill[g], 1ull);
+    const uint64_t d = keys[i];
+    gkey[pos] = d;
+    gamp[pos] = amps[i];
+    grank[pos] = str_rank(rank_tab, ks, even_bits(d >> 1));
+  }
+}
+
+}  // namespace
+
+size_t row_sweep_smem(int max_ent_s, int max_ent_d, int t_same, int touched_words) {
+  return sizeof(RowEnt) * (size_t)(max_ent_s + max_ent_d) + 4 * (size_t)t_same + 4 * (size_t)touched_words;
+}
+
+namespace {
+template <int NT>
+cudaError_t max_clusters_t(int gsz, size_t smem, int* n_clusters) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(gsz * 64);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = gsz;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaFuncSetAttribute(row_sweep_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (gsz > 8) {
+    e = cudaFuncSetAttribute(row_sweep_kernel<NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaOccupancyMaxActiveClusters(n_clusters, row_sweep_kernel<NT>, &cfg);
+}
+
+template <int NT>
+cudaError_t launch_t(const RowArgs& a, int gsz, int n_clusters, size_t smem, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(gsz * n_clusters);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = gsz;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, row_sweep_kernel<NT>, a);
+}
+}  // namespace
+
+cudaError_t row_sweep_max_clusters(int threads, int gsz, size_t smem, int* n_clusters) {
+  if (threads == 128) return max_clusters_t<128>(gsz, smem, n_clusters);
+  if (threads == 256) return max_clusters_t<256>(gsz, smem, n_clusters);
+  if (threads == 512) return max_clusters_t<512>(gsz, smem, n_clusters);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_row_sweep(const RowArgs& a, int threads, int gsz, int n_clusters, size_t smem, cudaStream_t st) {
+  if (threads == 128) return launch_t<128>(a, gsz, n_clusters, smem, st);
+  if (threads == 256) return launch_t<256>(a, gsz, n_clusters, smem, st);
+  if (threads == 512) return launch_t<512>(a, gsz, n_clusters, smem, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_group_state(const GroupArgs& g, cudaStream_t st) {
+  const int nb = 1216;
+  group_insert_kernel<<<nb, 256, 0, st>>>(g.keys, g.n, g.atab, g.amask, g.amps, g.acc);
+  group_ids_kernel<<<nb, 256, 0, st>>>(g.atab, g.amask + 1, g.n_groups);
+  group_count_kernel<<<nb, 256, 0, st>>>(g.keys, g.n, g.atab, g.amask, g.gid_of, g.gcount);
+  group_scan_kernel<<<1, 1024, 0, st>>>(g.gcount, g.n_groups, g.goff);
+  group_scatter_kernel<<<nb, 256, 0, st>>>(g.keys, g.amps, g.n, g.gid_of, g.goff, g.gfill, g.gkey, g.gamp, g.grank,
+                                           g.rank_tab, g.ks);
+  return cudaGetLastError();
+}
+
+}  // namespace swcs

@@ -56,6 +56,8 @@ _SIGS = {
     "swcs_profile_enable": ([_vp, _i], _i),
     "swcs_profile_read": ([_vp, _vp, _vp, _i], _i),
     "swcs_energy_noalloc": ([_vp, _vp, _vp, _i64, _vp], _i),
+    "swcs_set_option": ([_vp, ctypes.c_char_p, _i64], _i),
+    "swcs_sweep_energy": ([_vp, _pd, _pd], _i),
 }
 
 for _name, (_args, _res) in _SIGS.items():
@@ -208,6 +210,14 @@ class Context:
         amps = _c(amps, np.float64)
         self._ck(lib.swcs_set_state(self._h, _ptr(keys), _ptr(amps), len(keys)))
 
+    def sweep_energy(self):
+        e, n2 = ctypes.c_double(), ctypes.c_double()
+        self._ck(lib.swcs_sweep_energy(self._h, ctypes.byref(e), ctypes.byref(n2)))
+        return e.value, n2.value
+
+    def set_option(self, name, value):
+        self._ck(lib.swcs_set_option(self._h, name.encode(), int(value)))
+
     def energy_noalloc(self, d_keys, d_amps, d_out):
         """Energy of a state in caller-owned device tensors (no device allocation)."""
         self._ck(lib.swcs_energy_noalloc(self._h, _tptr(d_keys), _tptr(d_amps), int(d_keys.numel()), _tptr(d_out)))
@@ -219,7 +229,7 @@ class Context:
                 "kernel_launches", "phi_max", "gate_dets"]
         return dict(zip(keys, out.tolist()))
 
-    KINDS = ("ansatz", "energy", "sigma_scatter", "pool_gather", "table_clear", "other")
+    KINDS = ("ansatz", "energy", "sigma_scatter", "pool_gather", "table_clear", "other", "row_sweep", "group")
 
     def profile_enable(self, on=True):
         self._ck(lib.swcs_profile_enable(self._h, 1 if on else 0))

@@ -93,6 +93,27 @@ def test_energy_and_pool_gradient_truncated(S, n_so, n_e, n_ops, seed, n_keep):
     assert np.abs(gs[sub] - go[sub]).max() < TOL
 
 
+@pytest.mark.parametrize("sweep,cluster,threads", [(1, 4, 512), (2, 1, 128), (2, 2, 256), (2, 4, 512), (2, 8, 512),
+                                                   (2, 1, 512)])
+@pytest.mark.parametrize("n_so,n_e,n_ops,seed,n_keep", [(16, 6, 40, 102, 150), (24, 8, 40, 107, 400),
+                                                        (28, 8, 60, 104, 3000), (12, 4, 10, 1, 0)])
+def test_sweep_paths_match_oracle(S, sweep, cluster, threads, n_so, n_e, n_ops, seed, n_keep):
+    """Hashed external-sigma sweep and alpha-string row sweep, several launch shapes."""
+    w = I.small_case(n_so, n_e, n_ops, seed, n_keep=n_keep)
+    c = ctx_for(S, w)
+    c.set_option("sweep", sweep)
+    c.set_option("cluster", cluster)
+    c.set_option("threads", threads)
+    c.apply_ansatz(w.ops, w.theta, n_keep)
+    ko, ao = O.apply_ansatz(w.n_so, w.n_e, w.ops, w.theta, n_keep)
+    g = c.pool_gradients()
+    go = O.pool_gradients(w.n_so, w.h, w.g, ko, ao)
+    assert np.abs(g - go).max() < TOL
+    e, n2 = c.sweep_energy()
+    eo, n2o = O.energy(w.n_so, w.h, w.g, ko, ao)
+    assert abs(e - eo) < TOL and abs(n2 - n2o) < 1e-13
+
+
 def test_truncation_with_ties_and_zeros(S):
     w = I.small_case(20, 6, 1, 7)
     c = ctx_for(S, w)
@@ -195,3 +216,8 @@ def test_so28_e8_full_size(S):
     assert np.abs(g[sub] - go[sub]).max() < TOL
     # the energy from the sweep's by-product equals the sigma-int energy (two code paths)
     assert abs(e - O.energy(w.n_so, w.h, w.g, ko, ao)[0]) < TOL
+    assert abs(c.sweep_energy()[0] - e) < TOL
+    # both sweep paths agree at full size
+    c.set_option("sweep", 1)
+    g1 = c.pool_gradients()
+    assert np.abs(g1 - g).max() < TOL
