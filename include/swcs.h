@@ -172,9 +172,10 @@ int swcs_energy_noalloc(swcs_ctx* ctx, const uint64_t* d_keys, const double* d_a
 /* Per-kernel device time with CUDA events recorded on the context's stream
  * around each launch (off by default).  Kinds: 0 gate/select kernel,
  * 1 energy, 2 hashed sigma scatter, 3 hashed pool gather, 4 table clear,
- * 5 other, 6 alpha-string row sweep, 7 grouping of the state by alpha string.
- * swcs_profile_read synchronises, returns accumulated milliseconds and launch
- * counts per kind (8 entries each; NULL to skip) and, when reset != 0,
+ * 5 other, 6 alpha-string row sweep, 7 grouping of the state by alpha string,
+ * 8 adjoint gate.  swcs_profile_read synchronises, returns accumulated
+ * milliseconds and launch counts per kind (9 entries each; NULL to skip) and,
+ * when reset != 0,
  * clears them together with the swcs_stats counters. */
 int swcs_profile_enable(swcs_ctx* ctx, int on);
 int swcs_profile_read(swcs_ctx* ctx, double* h_ms8, int64_t* h_launches8, int reset);

@@ -59,33 +59,6 @@ __device__ __forceinline__ bool keep_entry(const SelState& s, uint64_t key, doub
   return (key >> s.kshift) <= (s.kprefix >> s.kshift);
 }
 
-struct GateOp {
-  int kind;
-  uint64_t mask_a;  // annihilated by tau
-  uint64_t mask_c;  // created by tau
-  int i0, i1, i2, i3;
-};
-
-__device__ __forceinline__ GateOp decode_op(const uint8_t* o) {
-  GateOp g;
-  g.kind = o[0];
-  g.i0 = o[1];
-  g.i1 = o[2];
-  g.i2 = o[3];
-  g.i3 = o[4];
-  if (g.kind == 1) {
-    g.mask_a = 1ull << g.i0;
-    g.mask_c = 1ull << g.i1;
-  } else if (g.kind == 2) {
-    g.mask_a = (1ull << g.i0) | (1ull << g.i1);
-    g.mask_c = (1ull << g.i2) | (1ull << g.i3);
-  } else {  // kind 0: identity (truncation only)
-    g.mask_a = 0;
-    g.mask_c = 0;
-  }
-  return g;
-}
-
 // Counters per gate, in a ring of 3 so that the next gate's set can be
 // reset while the current one is live.
 enum { kCtrExtra = 0, kCtrZero = 1, kCtrKept = 2, kCtrN = 4 };

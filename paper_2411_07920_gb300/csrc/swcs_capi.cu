@@ -62,6 +62,9 @@ struct swcs_ctx {
   int opt_rows_l2 = 0;  // cap concurrent rows to about half of L2
   int opt_threads = 512;  // threads per CTA of the row sweep
 
+  // adjoint: checkpoints, per-gate snapshots of one segment, sigma, nu, indices, gradient
+  DevBuf ck_keys, ck_amps, ck_n, sn_keys, sn_amps, sn_n, sigma, nu0, nu1, atab0, atab1, dth;
+
   // external sigma table
   DevBuf ext;
   uint64_t ext_cap = 0;
@@ -80,8 +83,8 @@ struct swcs_ctx {
   };
   std::vector<Ev> ev_pending;
   std::vector<cudaEvent_t> ev_free;
-  double prof_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  int64_t prof_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double prof_ms[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t prof_n[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   int64_t launches = 0;
 };
 
@@ -158,7 +161,7 @@ int ensure_pinned(swcs_ctx* c, size_t bytes) {
 Ctrl* ctrl(swcs_ctx* c) { return (Ctrl*)c->ctrl.p; }
 
 // Kernel kinds for swcs_profile_read.
-enum Kind { kKAnsatz = 0, kKEnergy = 1, kKScatter = 2, kKGather = 3, kKClear = 4, kKOther = 5, kKRow = 6, kKGroup = 7 };
+enum Kind { kKAnsatz = 0, kKEnergy = 1, kKScatter = 2, kKGather = 3, kKClear = 4, kKOther = 5, kKRow = 6, kKGroup = 7, kKAdjoint = 8 };
 
 cudaEvent_t take_event(swcs_ctx* c) {
   if (!c->ev_free.empty()) {
@@ -648,7 +651,9 @@ int swcs_destroy(swcs_ctx* c) {
   DevBuf* bufs[] = {&c->h, &c->J, &c->Ws, &c->G, &c->opd, &c->ops1, &c->gstage, &c->keys_a, &c->amps_a,
                     &c->keys_b, &c->amps_b, &c->tab0, &c->tab1, &c->ctrl, &c->ops_dev, &c->cs_dev,
                     &c->gdev, &c->subset_dev, &c->gsub, &c->ext, &c->alpha_list, &c->rank_tab, &c->atab,
-                    &c->gid_of, &c->gcount, &c->goff, &c->gfill, &c->gkey, &c->gamp, &c->grank, &c->rows};
+                    &c->gid_of, &c->gcount, &c->goff, &c->gfill, &c->gkey, &c->gamp, &c->grank, &c->rows,
+                    &c->ck_keys, &c->ck_amps, &c->ck_n, &c->sn_keys, &c->sn_amps, &c->sn_n, &c->sigma, &c->nu0,
+                    &c->nu1, &c->atab0, &c->atab1, &c->dth};
   for (DevBuf* b : bufs) release(*b);
   if (c->pin) cudaFreeHost(c->pin);
   for (auto& e : c->ev_pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
@@ -998,7 +1003,7 @@ int swcs_profile_read(swcs_ctx* c, double* ms8, int64_t* n8, int reset) {
     c->ev_free.push_back(e.b);
   }
   c->ev_pending.clear();
-  for (int i = 0; i < 8; ++i) {
+  for (int i = 0; i < 9; ++i) {
     if (ms8) ms8[i] = c->prof_ms[i];
     if (n8) n8[i] = c->prof_n[i];
     if (reset) {
@@ -1016,8 +1021,130 @@ int swcs_profile_read(swcs_ctx* c, double* ms8, int64_t* n8, int reset) {
 
 int swcs_energy_grad(swcs_ctx* c, const uint8_t* h_ops, const double* h_theta, int n_ops, int64_t n_keep,
                      int ckpt_every, double* h_e_out, double* h_dtheta_out) {
-  (void)h_ops; (void)h_theta; (void)n_ops; (void)n_keep; (void)ckpt_every; (void)h_e_out; (void)h_dtheta_out;
-  return fail(c, SWCS_ERR_INVALID_ARG, "swcs_energy_grad: not built yet");
+  int r = need_ham(c);
+  if (r) return r;
+  if (n_ops <= 0 || !h_ops || !h_theta) return fail(c, SWCS_ERR_INVALID_ARG, "energy_grad needs at least one gate");
+  if ((r = validate_ops(c, h_ops, n_ops))) return r;
+  const int ck = ckpt_every > 0 ? ckpt_every : 20;
+  const int ncp = (n_ops + ck - 1) / ck;
+  const int64_t ms = max_state_for(c, n_keep, n_ops, 1);
+  if (ms > ((int64_t)1 << 31)) return fail(c, SWCS_ERR_INVALID_ARG, "state bound too large: give n_keep");
+  if ((r = ensure_state_buffers(c, ms))) return r;
+  const int64_t stride = ms + 64;
+  const uint64_t tcap = c->tab_mask + 1;
+  if ((r = ensure(c, c->ck_keys, (size_t)(ncp + 1) * stride * 8)) || (r = ensure(c, c->ck_amps, (size_t)(ncp + 1) * stride * 8)) ||
+      (r = ensure(c, c->ck_n, (size_t)(ncp + 1) * 8)) || (r = ensure(c, c->sn_keys, (size_t)ck * stride * 8)) ||
+      (r = ensure(c, c->sn_amps, (size_t)ck * stride * 8)) || (r = ensure(c, c->sn_n, (size_t)ck * 8)) ||
+      (r = ensure(c, c->sigma, (size_t)stride * 8)) || (r = ensure(c, c->nu0, (size_t)stride * 8)) ||
+      (r = ensure(c, c->nu1, (size_t)stride * 8)) || (r = ensure(c, c->atab0, tcap * sizeof(IdxSlot))) ||
+      (r = ensure(c, c->atab1, tcap * sizeof(IdxSlot))) || (r = ensure(c, c->dth, (size_t)n_ops * 8)))
+    return r;
+  if ((r = upload_ops(c, h_ops, h_theta, n_ops))) return r;
+  Ctrl* k = ctrl(c);
+  uint64_t* ckk = (uint64_t*)c->ck_keys.p;
+  double* cka = (double*)c->ck_amps.p;
+  long long* ckn = (long long*)c->ck_n.p;
+  const uint8_t* dops = (const uint8_t*)c->ops_dev.p;
+  const double* dcs = (const double*)c->cs_dev.p;
+  auto save_slot = [&](int slot) -> int {
+    CK(cudaMemcpyAsync(ckk + (size_t)slot * stride, c->keys_a.p, stride * 8, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(cka + (size_t)slot * stride, c->amps_a.p, stride * 8, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(ckn + slot, &k->n_state, 8, cudaMemcpyDeviceToDevice, c->st));
+    return SWCS_OK;
+  };
+  auto load_slot = [&](int slot) -> int {
+    CK(cudaMemcpyAsync(c->keys_a.p, ckk + (size_t)slot * stride, stride * 8, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(c->amps_a.p, cka + (size_t)slot * stride, stride * 8, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(&k->n_state, ckn + slot, 8, cudaMemcpyDeviceToDevice, c->st));
+    return SWCS_OK;
+  };
+  // ---- forward with a checkpoint before every segment and after the last gate
+  {
+    const uint64_t hf = (c->ne >= 64) ? ~0ull : ((1ull << c->ne) - 1ull);
+    const double one = 1.0;
+    const long long n1 = 1;
+    CK(cudaMemcpyAsync(ckk, &hf, 8, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(cka, &one, 8, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(ckn, &n1, 8, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(&k->n_state, &n1, 8, cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));  // host staging above
+  }
+  for (int seg = 0; seg < ncp; ++seg) {
+    const int g0 = seg * ck, g1 = std::min(n_ops, g0 + ck);
+    if (seg > 0 && (r = save_slot(seg))) return r;
+    if ((r = run_gates(c, dops + 5 * g0, dcs + 2 * g0, g1 - g0, n_keep, seg == 0))) return r;
+  }
+  if ((r = save_slot(ncp))) return r;
+  // ---- energy, sigma and nu_M = P_M (H - E) psi_M on the final state
+  CK(cudaMemsetAsync(k->acc, 0, 16, c->st));
+  const int nblk = c->nsm * sigma_blocks_per_sm();
+  CK(launch_k(c, kKEnergy, [&] { return launch_energy_sigma(ham_dev(c), state_dev(c), k->acc, (double*)c->sigma.p, nblk, c->st); }));
+  IdxSlot* atab[2] = {(IdxSlot*)c->atab0.p, (IdxSlot*)c->atab1.p};
+  double* nu[2] = {(double*)c->nu0.p, (double*)c->nu1.p};
+  CK(launch_k(c, kKOther, [&] { return launch_nu_init((const double*)c->amps_a.p, (const double*)c->sigma.p, &k->n_state, k->acc, nu[0], c->st); }));
+  CK(launch_k(c, kKOther, [&] { return launch_build_index(ckk + (size_t)ncp * stride, ckn + ncp, atab[0], tcap - 1, c->st); }));
+  CK(cudaMemsetAsync(c->dth.p, 0, (size_t)n_ops * 8, c->st));
+  int cur = 0;
+  const int adj_blocks = c->nsm * 8;
+  // ---- backward, one segment at a time
+  for (int seg = ncp - 1; seg >= 0; --seg) {
+    const int g0 = seg * ck, g1 = std::min(n_ops, g0 + ck);
+    if ((r = load_slot(seg))) return r;
+    if (g1 - g0 > 1) {
+      if ((r = run_gates(c, dops + 5 * g0, dcs + 2 * g0, g1 - g0 - 1, n_keep, false, (uint64_t*)c->sn_keys.p,
+                         (double*)c->sn_amps.p, (long long*)c->sn_n.p, stride)))
+        return r;
+    }
+    for (int g = g1 - 1; g >= g0; --g) {
+      const uint64_t* keys_g;
+      const double* amps_g;
+      const long long* n_g;
+      if (g == g0) {
+        keys_g = ckk + (size_t)seg * stride;
+        amps_g = cka + (size_t)seg * stride;
+        n_g = ckn + seg;
+      } else {
+        keys_g = (const uint64_t*)c->sn_keys.p + (size_t)(g - g0 - 1) * stride;
+        amps_g = (const double*)c->sn_amps.p + (size_t)(g - g0 - 1) * stride;
+        n_g = (const long long*)c->sn_n.p + (g - g0 - 1);
+      }
+      CK(launch_k(c, kKOther, [&] { return launch_build_index(keys_g, n_g, atab[cur ^ 1], tcap - 1, c->st); }));
+      AdjArgs a;
+      a.op = dops + 5 * g;
+      a.cs = dcs + 2 * g;
+      a.keys = keys_g;
+      a.amps = amps_g;
+      a.n = n_g;
+      a.tab = atab[cur ^ 1];
+      a.mask = tcap - 1;
+      a.tab_nu = atab[cur];
+      a.mask_nu = tcap - 1;
+      a.nu_in = nu[cur];
+      a.nu_out = nu[cur ^ 1];
+      a.dtheta = (double*)c->dth.p + g;
+      CK(launch_k(c, kKAdjoint, [&] { return launch_adjoint_gate(a, adj_blocks, c->st); }));
+      cur ^= 1;
+    }
+  }
+  CK(launch_k(c, kKOther, [&] { return launch_scale_dtheta((double*)c->dth.p, n_ops, k->acc, c->st); }));
+  CK(launch_k(c, kKOther, [&] { return launch_finalize_energy(k->acc, k->eout, c->st); }));
+  // leave psi_M as the context's state (index table rebuilt by an identity pass)
+  if ((r = load_slot(ncp))) return r;
+  {
+    const uint8_t id[5] = {0, 0, 0, 0, 0};
+    if ((r = ensure(c, c->gsub, 16))) return r;
+    CK(cudaMemcpyAsync(c->gsub.p, id, 5, cudaMemcpyHostToDevice, c->st));
+    const double z[2] = {1.0, 0.0};
+    if ((r = ensure(c, c->subset_dev, 16))) return r;
+    CK(cudaMemcpyAsync(c->subset_dev.p, z, 16, cudaMemcpyHostToDevice, c->st));
+    if ((r = run_gates(c, (const uint8_t*)c->gsub.p, (const double*)c->subset_dev.p, 1, 0, false))) return r;
+  }
+  double out[2];
+  CK(cudaMemcpyAsync(out, k->eout, 16, cudaMemcpyDeviceToHost, c->st));
+  if (h_dtheta_out) CK(cudaMemcpyAsync(h_dtheta_out, c->dth.p, (size_t)n_ops * 8, cudaMemcpyDeviceToHost, c->st));
+  if ((r = check_device(c, "swcs_energy_grad"))) return r;
+  if (h_e_out) *h_e_out = out[0];
+  return SWCS_OK;
 }
 
 }  // extern "C"

@@ -102,6 +102,50 @@ __device__ __forceinline__ int double_phase(uint64_t d, int a0, int a1, int c2, 
 __device__ __forceinline__ double apply_sign(double v, int sign_bit) { return sign_bit ? -v : v; }
 
 // ----------------------------------------------------------------------------
+// A gate operator (5 bytes: kind, i0..i3; kind 1: tau = a+_{i1} a_{i0},
+// kind 2: tau = a+_{i2} a+_{i3} a_{i1} a_{i0}, kind 0: identity).
+// ----------------------------------------------------------------------------
+struct GateOp {
+  int kind;
+  uint64_t mask_a;  // annihilated by tau
+  uint64_t mask_c;  // created by tau
+  int i0, i1, i2, i3;
+};
+
+__device__ __forceinline__ GateOp decode_op(const uint8_t* o) {
+  GateOp g;
+  g.kind = o[0];
+  g.i0 = o[1];
+  g.i1 = o[2];
+  g.i2 = o[3];
+  g.i3 = o[4];
+  if (g.kind == 1) {
+    g.mask_a = 1ull << g.i0;
+    g.mask_c = 1ull << g.i1;
+  } else if (g.kind == 2) {
+    g.mask_a = (1ull << g.i0) | (1ull << g.i1);
+    g.mask_c = (1ull << g.i2) | (1ull << g.i3);
+  } else {
+    g.mask_a = 0;
+    g.mask_c = 0;
+  }
+  return g;
+}
+
+// Role of d under the gate: +1 lower (tau d != 0), -1 upper (tau^dag d != 0),
+// 0 neither.  *partner and *sbit (phase of tau d, or of tau^dag d) on +-1.
+__device__ __forceinline__ int gate_role(const GateOp& op, uint64_t d, uint64_t* partner, int* sbit) {
+  if (!op.kind) return 0;
+  const bool up = ((d & op.mask_a) == op.mask_a) && ((d & op.mask_c) == 0);
+  const bool dn = ((d & op.mask_c) == op.mask_c) && ((d & op.mask_a) == 0);
+  if (!up && !dn) return 0;
+  *partner = d ^ op.mask_a ^ op.mask_c;
+  if (op.kind == 1) *sbit = up ? single_phase(d, op.i0, op.i1) : single_phase(d, op.i1, op.i0);
+  else *sbit = up ? double_phase(d, op.i0, op.i1, op.i2, op.i3) : double_phase(d, op.i2, op.i3, op.i0, op.i1);
+  return up ? 1 : -1;
+}
+
+// ----------------------------------------------------------------------------
 // Global timer and bounded waits.
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t globaltimer_ns() {

@@ -83,6 +83,9 @@ struct ExtTable {
 
 // Energy (sigma restricted to S): acc[0] += sum c_D sigma_D, acc[1] += sum c_D^2.
 cudaError_t launch_energy(const HamDev& H, const StateDev& S, double* acc, int nblocks, cudaStream_t st);
+// Energy as above and sigma_D for each determinant of S (state order) into sig_out.
+cudaError_t launch_energy_sigma(const HamDev& H, const StateDev& S, double* acc, double* sig_out, int nblocks,
+                                cudaStream_t st);
 // Pool sweep pass 1: sigma_E += <E|H|D> c_D for E in bucket.
 cudaError_t launch_sigma_scatter(const HamDev& H, const StateDev& S, const ExtTable& T, int nblocks,
                                  cudaStream_t st);
@@ -140,6 +143,27 @@ size_t row_sweep_smem(int max_ent_s, int max_ent_d, int t_same, int touched_word
 cudaError_t row_sweep_max_clusters(int threads, int gsz, size_t smem, int* n_clusters);
 cudaError_t launch_row_sweep(const RowArgs& a, int threads, int gsz, int n_clusters, size_t smem, cudaStream_t st);
 cudaError_t launch_group_state(const GroupArgs& g, cudaStream_t st);
+
+// Adjoint (swcs_adjoint.cu).
+cudaError_t launch_build_index(const uint64_t* keys, const long long* n, IdxSlot* tab, uint64_t mask, cudaStream_t st);
+cudaError_t launch_nu_init(const double* amps, const double* sigma, const long long* n, const double* acc, double* nu,
+                           cudaStream_t st);
+struct AdjArgs {
+  const uint8_t* op;     // this gate
+  const double* cs;      // its (cos, sin)
+  const uint64_t* keys;  // S_g (before the gate), with its index table
+  const double* amps;
+  const long long* n;
+  const IdxSlot* tab;
+  uint64_t mask;
+  const IdxSlot* tab_nu;  // index of the arrays nu_in is aligned with (S_{g+1})
+  uint64_t mask_nu;
+  const double* nu_in;
+  double* nu_out;         // aligned with S_g
+  double* dtheta;         // accumulates the (unscaled) gradient of this gate
+};
+cudaError_t launch_adjoint_gate(const AdjArgs& a, int nblocks, cudaStream_t st);
+cudaError_t launch_scale_dtheta(double* d, int n, const double* acc, cudaStream_t st);
 
 // Hamiltonian preparation from the full <pq||rs> array on the device.
 cudaError_t launch_pack_hamiltonian(const double* g_full, int n, double* J, double* Ws, double* G,

@@ -166,7 +166,7 @@ __device__ __forceinline__ void visit_single(PairCtx<MODE>& x, const WarpLists& 
 
 template <int MODE>
 __global__ void __launch_bounds__(kSigmaThreads)
-sigma_kernel(HamDev H, StateDev S, ExtTable T, double* g, double* acc_out, int add_norm) {
+sigma_kernel(HamDev H, StateDev S, ExtTable T, double* g, double* acc_out, int add_norm, double* sig_out) {
   __shared__ WarpLists lists[kWarps];
   __shared__ Tables tabs;
   __shared__ double s_red[2][kWarps];
@@ -267,6 +267,7 @@ sigma_kernel(HamDev H, StateDev S, ExtTable T, double* g, double* acc_out, int a
       if (lane == 0) {
         e_num += cd * (hd * cd + off);
         e_n2 += cd * cd;
+        if (sig_out) sig_out[i] = hd * cd + off;
       }
     } else if (MODE == kScatter) {
       if (lane == 0) {
@@ -304,7 +305,7 @@ sigma_kernel(HamDev H, StateDev S, ExtTable T, double* g, double* acc_out, int a
     for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
     if (lane == 0 && w) atomicAdd(&s_new, w);
   }
-  if (my_fail) set_error(T.err ? T.err : nullptr, kDevTableFull);
+  if (my_fail && T.err) set_error(T.err, kDevTableFull);
   if (MODE != kScatter) {
     if (lane == 0) {
       s_red[0][warp] = e_num;
@@ -388,19 +389,26 @@ int sigma_blocks_per_sm() {
 
 cudaError_t launch_energy(const HamDev& H, const StateDev& S, double* acc, int nblocks, cudaStream_t st) {
   ExtTable T{};
-  sigma_kernel<kEnergy><<<nblocks, kSigmaThreads, 0, st>>>(H, S, T, nullptr, acc, 1);
+  sigma_kernel<kEnergy><<<nblocks, kSigmaThreads, 0, st>>>(H, S, T, nullptr, acc, 1, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_sigma(const HamDev& H, const StateDev& S, double* acc, double* sig_out, int nblocks,
+                                cudaStream_t st) {
+  ExtTable T{};
+  sigma_kernel<kEnergy><<<nblocks, kSigmaThreads, 0, st>>>(H, S, T, nullptr, acc, 1, sig_out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sigma_scatter(const HamDev& H, const StateDev& S, const ExtTable& T, int nblocks,
                                  cudaStream_t st) {
-  sigma_kernel<kScatter><<<nblocks, kSigmaThreads, 0, st>>>(H, S, T, nullptr, nullptr, 0);
+  sigma_kernel<kScatter><<<nblocks, kSigmaThreads, 0, st>>>(H, S, T, nullptr, nullptr, 0, nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pool_gather(const HamDev& H, const StateDev& S, const ExtTable& T, double* g, double* acc,
                                int add_norm, int nblocks, cudaStream_t st) {
-  sigma_kernel<kGather><<<nblocks, kSigmaThreads, 0, st>>>(H, S, T, g, acc, add_norm);
+  sigma_kernel<kGather><<<nblocks, kSigmaThreads, 0, st>>>(H, S, T, g, acc, add_norm, nullptr);
   return cudaGetLastError();
 }
 

@@ -229,13 +229,14 @@ class Context:
                 "kernel_launches", "phi_max", "gate_dets"]
         return dict(zip(keys, out.tolist()))
 
-    KINDS = ("ansatz", "energy", "sigma_scatter", "pool_gather", "table_clear", "other", "row_sweep", "group")
+    KINDS = ("ansatz", "energy", "sigma_scatter", "pool_gather", "table_clear", "other", "row_sweep", "group",
+             "adjoint")
 
     def profile_enable(self, on=True):
         self._ck(lib.swcs_profile_enable(self._h, 1 if on else 0))
 
     def profile_read(self, reset=True):
-        ms = np.zeros(8)
-        n = np.zeros(8, np.int64)
+        ms = np.zeros(9)
+        n = np.zeros(9, np.int64)
         self._ck(lib.swcs_profile_read(self._h, _ptr(ms), _ptr(n), 1 if reset else 0))
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.KINDS)}
