@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--cluster", type=int, default=2, help="CTAs per alpha-string row cluster")
     p.add_argument("--rows-l2", type=int, default=0, help="1: cap concurrent rows to about half of L2")
     p.add_argument("--threads", type=int, default=512, help="threads per CTA of the row sweep")
+    p.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched leg")
+    p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     return p.parse_args()
 
 
@@ -303,6 +305,23 @@ def run_swcs(args):
         e2e = {"value": world * args.steps / t_e2e, "unit": "sweeps/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
+    # ------------------------------------------------------------ adjoint leg (same workload, 200 parameters)
+    adjoint = None
+    if not args.no_adjoint:
+        ts = []
+        for it in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e_adj, d_adj = ctx.energy_grad(w.ops, w.theta, args.n_keep, 20)
+            ts.append(time.perf_counter() - t0)
+        adjoint = {"ms": round(1e3 * min(ts[1:]), 3), "params": int(len(w.theta)), "ckpt_every": 20,
+                   "energy": e_adj, "grad_norm": float(np.linalg.norm(d_adj))}
+
+    # ------------------------------------------------------------ batched leg: 64 uneven instances
+    batch = None
+    if not args.no_batch:
+        batch = run_batch_leg(swcs, I, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle as O
@@ -321,6 +340,7 @@ def run_swcs(args):
                            "parallelism": f"replicas x{world}", "l2": "flushed between steps (512 MB write)"},
                 "gate_dets_per_s": gate_dets_per_s, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "energy_ms": round(min(energy_ms), 3),
+                "adjoint": adjoint, "batch": batch,
                 "kernels_ms": {k: round(v[0], 3) for k, v in prof.items()},
                 "ext": {"distinct": stats["ext_distinct"], "buckets": stats["ext_buckets"],
                         "capacity": stats["ext_capacity"]}}
@@ -328,6 +348,61 @@ def run_swcs(args):
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_batch_leg(swcs, I, torch, n_inst=64, seed0=100, reps=3):
+    """64 uneven instances (n_so in U{16..40}, n_e in U{4..12}, 20-150 gates,
+    N_keep log-uniform 1e3-1e5): one autotuned graph launch for all of them
+    against the plain path (one context per instance, apply + pool sweep
+    through the host API, one instance after another)."""
+    specs = I.batch_specs(n_inst, seed0)
+    ws = [I.batch_instance(s) for s in specs]
+    b = swcs.Batch()
+    for w in ws:
+        b.add(w.h, w.g, w.n_so, w.n_e, w.ops, w.theta, w.n_keep)
+    b.build(autotune=True)
+    b.run()
+    b.results(0)
+    tg = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.run()
+        b.results(0)  # synchronises
+        tg.append(time.perf_counter() - t0)
+    ctxs = []
+    for w in ws:
+        c = swcs.Context()
+        c.load_hamiltonian(w.h, w.g, w.n_so, w.n_e)
+        ctxs.append(c)
+
+    def serial():
+        for c, w in zip(ctxs, ws):
+            c.apply_ansatz(w.ops, w.theta, w.n_keep)
+            c.pool_gradients()
+            c.sweep_energy()
+
+    serial()
+    ts = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        serial()
+        ts.append(time.perf_counter() - t0)
+    # the two paths agree
+    err = 0.0
+    for i in (0, n_inst // 2, n_inst - 1):
+        e, _, g = b.results(i)
+        ctxs[i].apply_ansatz(ws[i].ops, ws[i].theta, ws[i].n_keep)
+        g1 = ctxs[i].pool_gradients()
+        err = max(err, float(np.abs(g - g1).max()), abs(e - ctxs[i].sweep_energy()[0]))
+    tun = b.tuning()
+    for c in ctxs:
+        c.close()
+    b.close()
+    return {"instances": n_inst, "graph_ms": round(1e3 * min(tg), 3), "serial_ms": round(1e3 * min(ts), 3),
+            "speedup": round(min(ts) / min(tg), 3), "max_abs_diff": err, "autotune": tun,
+            "instances_per_s": round(n_inst / min(tg), 3)}
 
 
 def main():

@@ -142,6 +142,8 @@ int swcs_stats(swcs_ctx* ctx, int64_t* h_out8);
  *              beta-string space exceeds 2^22 or clusters cannot launch)
  *   "cluster"  CTAs per alpha-string row in the row sweep, 1..16 (default 2)
  *   "threads"  threads per CTA of the row sweep: 128, 256 or 512 (default 512)
+ *   "gate_blocks"   CTAs of the persistent gate kernel (0, default: whole device)
+ *   "row_clusters"  clusters of the row sweep (0, default: as many as fit)
  *   "rows_l2"  1: cap the row sweep's concurrent rows to about half of L2;
  *              0 (default): as many rows as clusters fit on the device */
 int swcs_set_option(swcs_ctx* ctx, const char* name, int64_t value);
@@ -179,6 +181,35 @@ int swcs_energy_noalloc(swcs_ctx* ctx, const uint64_t* d_keys, const double* d_a
  * clears them together with the swcs_stats counters. */
 int swcs_profile_enable(swcs_ctx* ctx, int on);
 int swcs_profile_read(swcs_ctx* ctx, double* h_ms8, int64_t* h_launches8, int reset);
+
+/* Batched launch: many independent instances (each its own Hamiltonian,
+ * ansatz and N_keep) evaluated together -- ansatz, energy and full pool
+ * gradient -- by one CUDA graph launch.  Each instance's pipeline (persistent
+ * gate kernel, alpha-string grouping, row sweep, finalisation) runs on its own
+ * branch of the graph with a share of the device proportional to its work.
+ *   swcs_batch_add     copies the inputs (same meaning as swcs_load_hamiltonian
+ *                      and swcs_apply_ansatz); *index_out = instance index
+ *   swcs_batch_build   sizes every buffer and captures the graph; autotune != 0
+ *                      first times candidate device shares and row-sweep
+ *                      cluster sizes on the whole graph and keeps the fastest
+ *   swcs_batch_run     one cudaGraphLaunch on the stream given at creation (when
+ *                      that is NULL, on a blocking stream owned by the batch)
+ *   swcs_batch_results synchronises; E, <psi|psi> and the pool gradient
+ *                      (swcs_batch_pool_size entries) of instance i
+ *   swcs_batch_tuning  {device share, cluster size, tuned graph ms, instances}
+ * Instances whose beta-string space exceeds 2^22 are rejected at build. */
+typedef struct swcs_batch swcs_batch;
+int swcs_batch_create(swcs_batch** out, void* cuda_stream);
+int swcs_batch_destroy(swcs_batch* b);
+const char* swcs_batch_last_error(const swcs_batch* b);
+int swcs_batch_add(swcs_batch* b, const double* h_h, const double* h_g, int n_so, int n_elec, const uint8_t* h_ops,
+                   const double* h_theta, int n_ops, int64_t n_keep, int* index_out);
+int swcs_batch_build(swcs_batch* b, int autotune);
+int swcs_batch_run(swcs_batch* b);
+int swcs_batch_size(swcs_batch* b, int* n_out);
+int swcs_batch_pool_size(swcs_batch* b, int i, int64_t* n_out);
+int swcs_batch_results(swcs_batch* b, int i, double* h_e, double* h_norm2, double* h_g);
+int swcs_batch_tuning(swcs_batch* b, double* h_out4);
 
 #ifdef __cplusplus
 }

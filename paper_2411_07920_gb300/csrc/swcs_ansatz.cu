@@ -297,9 +297,18 @@ int ansatz_blocks_per_sm() {
 }
 
 cudaError_t launch_ansatz(const AnsatzArgs& args, int nblocks, cudaStream_t st) {
-  AnsatzArgs a = args;
-  void* params[] = {&a};
-  return cudaLaunchCooperativeKernel((const void*)ansatz_kernel, dim3(nblocks), dim3(kAnsatzThreads), params, 0, st);
+  // cooperative launch (all CTAs co-resident, as the grid barrier needs); the
+  // launch-attribute form is also valid inside stream capture
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nblocks);
+  cfg.blockDim = dim3(kAnsatzThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, ansatz_kernel, args);
 }
 
 }  // namespace swcs

@@ -61,6 +61,8 @@ struct swcs_ctx {
   int opt_cluster = 2;  // CTAs per row cluster
   int opt_rows_l2 = 0;  // cap concurrent rows to about half of L2
   int opt_threads = 512;  // threads per CTA of the row sweep
+  int opt_gate_blocks = 0;   // CTAs of the gate kernel (0: whole device)
+  int opt_row_clusters = 0;  // clusters of the row sweep (0: as many as fit)
 
   // adjoint: checkpoints, per-gate snapshots of one segment, sigma, nu, indices, gradient
   DevBuf ck_keys, ck_amps, ck_n, sn_keys, sn_amps, sn_n, sigma, nu0, nu1, atab0, atab1, dth;
@@ -372,7 +374,9 @@ int run_gates(swcs_ctx* c, const uint8_t* d_ops, const double* d_cs, int n_ops, 
   a.stats = k->stats;
   // barrier words must start at zero
   CK(cudaMemsetAsync(&k->bar, 0, sizeof(GridBar), c->st));
-  CK(launch_k(c, kKAnsatz, [&] { return launch_ansatz(a, c->nsm * bps, c->st); }));
+  int nblocks = c->nsm * bps;
+  if (c->opt_gate_blocks > 0) nblocks = std::min(nblocks, c->opt_gate_blocks);
+  CK(launch_k(c, kKAnsatz, [&] { return launch_ansatz(a, nblocks, c->st); }));
   c->tab_cur = (int)(((unsigned)n_ops) & 1u);  // the kernel rebuilds tab[0] for the input, swaps per gate
   c->have_state = true;
   c->n_state_host = -1;
@@ -430,10 +434,12 @@ __global__ void sincos_kernel(const double* th, double* cs, int n) {
 }
 
 // Alpha-string row sweep; returns 1 when not applicable (caller falls back).
-int sweep_rows(swcs_ctx* c, double* d_g) {
+// nd_bound >= 0: size buffers for that many determinants instead of reading
+// the state size (no host synchronisation); enqueue = false: only size.
+int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = true) {
   const int m = c->n / 2;
   if (m > 32 || c->NB <= 0 || c->NB > (1 << 22)) return 1;
-  const int64_t nd = host_state_size(c);
+  const int64_t nd = nd_bound >= 0 ? nd_bound : host_state_size(c);
   if (nd < 0) return fail(c, SWCS_ERR_CUDA, "cannot read state size");
   Ctrl* k = ctrl(c);
   const int gsz = std::max(1, std::min(16, c->opt_cluster));
@@ -460,6 +466,7 @@ int sweep_rows(swcs_ctx* c, double* d_g) {
   const int64_t row_bytes = c->NB * 8;
   const int l2_rows = (int)std::max<int64_t>(1, (int64_t)l2 / 2 / std::max<int64_t>(row_bytes, 1));
   if (c->opt_rows_l2 && ncl > l2_rows) ncl = l2_rows;
+  if (c->opt_row_clusters > 0 && ncl > c->opt_row_clusters) ncl = c->opt_row_clusters;
   int r;
   const uint64_t acap = pow2_at_least((uint64_t)std::max<int64_t>(2 * nd, 64));
   if ((r = ensure(c, c->atab, acap * sizeof(IdxSlot))) || (r = ensure(c, c->gid_of, nd * 4 + 4)) ||
@@ -468,6 +475,7 @@ int sweep_rows(swcs_ctx* c, double* d_g) {
       (r = ensure(c, c->gamp, nd * 8 + 8)) || (r = ensure(c, c->grank, nd * 4 + 4)) ||
       (r = ensure(c, c->rows, (size_t)ncl * c->NB * 8)))
     return r;
+  if (!enqueue) return SWCS_OK;
   CK(cudaMemsetAsync(c->atab.p, 0xff, acap * sizeof(IdxSlot), c->st));
   CK(cudaMemsetAsync(c->gcount.p, 0, nd * 8 + 8, c->st));
   CK(cudaMemsetAsync(c->gfill.p, 0, nd * 8 + 8, c->st));
@@ -970,6 +978,12 @@ int swcs_set_option(swcs_ctx* c, const char* name, int64_t value) {
   if (k == "sweep") {
     if (value < 0 || value > 2) return fail(c, SWCS_ERR_INVALID_ARG, "sweep must be 0, 1 or 2");
     c->opt_sweep = (int)value;
+  } else if (k == "gate_blocks") {
+    if (value < 0) return fail(c, SWCS_ERR_INVALID_ARG, "gate_blocks must be >= 0");
+    c->opt_gate_blocks = (int)value;
+  } else if (k == "row_clusters") {
+    if (value < 0) return fail(c, SWCS_ERR_INVALID_ARG, "row_clusters must be >= 0");
+    c->opt_row_clusters = (int)value;
   } else if (k == "threads") {
     if (value != 128 && value != 256 && value != 512) return fail(c, SWCS_ERR_INVALID_ARG, "threads must be 128, 256 or 512");
     c->opt_threads = (int)value;
@@ -1144,6 +1158,271 @@ int swcs_energy_grad(swcs_ctx* c, const uint8_t* h_ops, const double* h_theta, i
   if (h_dtheta_out) CK(cudaMemcpyAsync(h_dtheta_out, c->dth.p, (size_t)n_ops * 8, cudaMemcpyDeviceToHost, c->st));
   if ((r = check_device(c, "swcs_energy_grad"))) return r;
   if (h_e_out) *h_e_out = out[0];
+  return SWCS_OK;
+}
+
+
+// =============================================================================
+// Batched launch: many independent instances in one CUDA graph.
+// =============================================================================
+struct swcs_batch {
+  cudaStream_t origin = nullptr;
+  bool own_origin = false;  // created here: the legacy default stream cannot be captured
+  int dev = 0;
+  std::string err;
+  std::vector<swcs_ctx*> inst;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> done;
+  std::vector<int64_t> n_keep, max_state;
+  std::vector<int> n_ops;
+  cudaEvent_t fork = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double share = 1.0;
+  int cluster = 2;
+  float tuned_ms = 0.f;
+};
+
+namespace {
+
+int bfail(swcs_batch* b, int code, const std::string& msg) {
+  if (b) b->err = msg;
+  return code;
+}
+
+void batch_drop_graph(swcs_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+// Work of an instance: gate applications + connected pairs of its sweep.
+double inst_work(swcs_ctx* c, int n_ops, int64_t ms) {
+  const double nconn = 2.0 * c->no * c->nv + 2.0 * binom(c->no, 2) * binom(c->nv, 2) + (double)c->no * c->no * c->nv * c->nv;
+  return (double)n_ops * (double)ms + (double)ms * (nconn + 1.0);
+}
+
+// Captures every instance's pipeline (persistent gate kernel, grouping, row
+// sweep, finalisation) on its own stream branch; grid sizes are the
+// instance's share of the device, proportional to its work.
+int batch_capture(swcs_batch* b, double share, int cluster) {
+  batch_drop_graph(b);
+  const int n = (int)b->inst.size();
+  double wsum = 0.0;
+  std::vector<double> w(n);
+  for (int i = 0; i < n; ++i) wsum += (w[i] = inst_work(b->inst[i], b->n_ops[i], b->max_state[i]));
+  swcs_ctx* c0 = b->inst[0];
+  const int gate_total = c0->nsm * std::max(1, ansatz_blocks_per_sm());
+  for (int i = 0; i < n; ++i) {
+    swcs_ctx* c = b->inst[i];
+    const double f = std::min(1.0, share * w[i] / wsum);
+    c->opt_gate_blocks = std::max(1, (int)std::lround(f * gate_total));
+    c->opt_cluster = cluster;
+    c->opt_row_clusters = std::max(1, (int)std::lround(f * gate_total / (2.0 * cluster)));
+    int r = sweep_rows(c, (double*)c->gdev.p, b->max_state[i], false);  // size only
+    if (r == 1) return bfail(b, SWCS_ERR_INVALID_ARG, "batch: an instance's sector does not fit the row sweep");
+    if (r) return bfail(b, r, std::string("batch sizing: ") + c->err);
+  }
+  cudaError_t e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return bfail(b, SWCS_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+  cudaEventRecord(b->fork, b->origin);
+  int status = SWCS_OK;
+  for (int i = 0; i < n && status == SWCS_OK; ++i) {
+    swcs_ctx* c = b->inst[i];
+    cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+    int r = run_gates(c, (const uint8_t*)c->ops_dev.p, (const double*)c->cs_dev.p, b->n_ops[i], b->n_keep[i], true);
+    if (!r) r = sweep_rows(c, (double*)c->gdev.p, b->max_state[i], true);
+    if (r) {
+      status = bfail(b, r == 1 ? SWCS_ERR_INVALID_ARG : r, std::string("batch capture: ") + c->err);
+      break;
+    }
+    cudaEventRecord(b->done[i], b->streams[i]);
+    cudaStreamWaitEvent(b->origin, b->done[i], 0);
+  }
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(b->origin, &g);
+  if (status) {
+    if (g) cudaGraphDestroy(g);
+    return status;
+  }
+  if (e != cudaSuccess) return bfail(b, SWCS_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e));
+  b->graph = g;
+  e = cudaGraphInstantiate(&b->exec, g, 0);
+  if (e != cudaSuccess) return bfail(b, SWCS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  for (int i = 0; i < n; ++i) b->inst[i]->have_state = true;
+  return SWCS_OK;
+}
+
+int batch_check(swcs_batch* b) {
+  cudaError_t e = cudaStreamSynchronize(b->origin);
+  if (e != cudaSuccess) return bfail(b, SWCS_ERR_CUDA, std::string("batch run: ") + cudaGetErrorString(e));
+  for (swcs_ctx* c : b->inst) {
+    int r = check_device(c, "batch instance");
+    if (r) return bfail(b, r, c->err);
+  }
+  return SWCS_OK;
+}
+
+}  // namespace
+
+int swcs_batch_create(swcs_batch** out, void* cuda_stream) {
+  if (!out) return SWCS_ERR_INVALID_ARG;
+  swcs_batch* b = new swcs_batch();
+  b->origin = (cudaStream_t)cuda_stream;
+  if (cudaGetDevice(&b->dev) != cudaSuccess || cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+    delete b;
+    return SWCS_ERR_NO_DEVICE;
+  }
+  if (!b->origin) {  // a blocking stream: ordered with the legacy default stream
+    if (cudaStreamCreate(&b->origin) != cudaSuccess) {
+      cudaEventDestroy(b->fork);
+      delete b;
+      return SWCS_ERR_CUDA;
+    }
+    b->own_origin = true;
+  }
+  *out = b;
+  return SWCS_OK;
+}
+
+int swcs_batch_destroy(swcs_batch* b) {
+  if (!b) return SWCS_OK;
+  cudaStreamSynchronize(b->origin);
+  batch_drop_graph(b);
+  for (swcs_ctx* c : b->inst) swcs_destroy(c);
+  for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->done) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->own_origin) cudaStreamDestroy(b->origin);
+  delete b;
+  return SWCS_OK;
+}
+
+const char* swcs_batch_last_error(const swcs_batch* b) { return b ? b->err.c_str() : "no batch"; }
+
+int swcs_batch_add(swcs_batch* b, const double* h_h, const double* h_g, int n_so, int n_elec, const uint8_t* h_ops,
+                   const double* h_theta, int n_ops, int64_t n_keep, int* index_out) {
+  if (!b) return SWCS_ERR_INVALID_ARG;
+  if (n_ops <= 0 || !h_ops || !h_theta) return bfail(b, SWCS_ERR_INVALID_ARG, "batch_add: needs at least one gate");
+  cudaStream_t st;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+    return bfail(b, SWCS_ERR_CUDA, "batch_add: stream creation failed");
+  swcs_ctx* c = nullptr;
+  int r = swcs_create(&c, st);
+  if (r) {
+    cudaStreamDestroy(st);
+    return bfail(b, r, "batch_add: context creation failed");
+  }
+  auto undo = [&](int code) {
+    const std::string m = c->err;
+    swcs_destroy(c);
+    cudaStreamDestroy(st);
+    return bfail(b, code, "batch_add: " + m);
+  };
+  if ((r = swcs_load_hamiltonian(c, h_h, h_g, n_so, n_elec))) return undo(r);
+  if ((r = validate_ops(c, h_ops, n_ops))) return undo(r);
+  const int64_t ms = max_state_for(c, n_keep, n_ops, 1);
+  if (ms > ((int64_t)1 << 31)) return undo(fail(c, SWCS_ERR_INVALID_ARG, "state bound too large: give n_keep"));
+  if ((r = ensure_state_buffers(c, ms)) || (r = upload_ops(c, h_ops, h_theta, n_ops)) ||
+      (r = ensure(c, c->gdev, sizeof(double) * c->pool_size)))
+    return undo(r);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return undo(SWCS_ERR_CUDA);
+  cudaEvent_t ev;
+  cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  b->inst.push_back(c);
+  b->streams.push_back(st);
+  b->done.push_back(ev);
+  b->n_keep.push_back(n_keep);
+  b->max_state.push_back(ms);
+  b->n_ops.push_back(n_ops);
+  batch_drop_graph(b);
+  if (index_out) *index_out = (int)b->inst.size() - 1;
+  return SWCS_OK;
+}
+
+int swcs_batch_build(swcs_batch* b, int autotune) {
+  if (!b || b->inst.empty()) return bfail(b, SWCS_ERR_INVALID_ARG, "batch_build: no instances");
+  if (!autotune) return batch_capture(b, b->share, b->cluster);
+  // autotuner: device share per unit of work and cluster size of the row
+  // sweep, timed on the whole graph
+  const double shares[] = {1.0, 2.0, 4.0, 8.0};
+  const int clusters[] = {1, 2};
+  double best_ms = 1e30, best_share = 1.0;
+  int best_cl = 2;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (double sh : shares)
+    for (int cl : clusters) {
+      int r = batch_capture(b, sh, cl);
+      if (r) continue;
+      cudaGraphLaunch(b->exec, b->origin);  // warm-up
+      if (batch_check(b)) continue;
+      float best = 1e30f;
+      for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0, b->origin);
+        cudaGraphLaunch(b->exec, b->origin);
+        cudaEventRecord(e1, b->origin);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        best = std::min(best, ms);
+      }
+      if (best < best_ms) {
+        best_ms = best;
+        best_share = sh;
+        best_cl = cl;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best_ms >= 1e30) return bfail(b, SWCS_ERR_CUDA, "batch autotune: no configuration ran");
+  b->share = best_share;
+  b->cluster = best_cl;
+  b->tuned_ms = (float)best_ms;
+  return batch_capture(b, best_share, best_cl);
+}
+
+int swcs_batch_run(swcs_batch* b) {
+  if (!b || !b->exec) return bfail(b, SWCS_ERR_INVALID_ARG, "batch_run: call swcs_batch_build first");
+  const cudaError_t e = cudaGraphLaunch(b->exec, b->origin);
+  if (e != cudaSuccess) return bfail(b, SWCS_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  return SWCS_OK;
+}
+
+int swcs_batch_size(swcs_batch* b, int* n_out) {
+  if (!b || !n_out) return SWCS_ERR_INVALID_ARG;
+  *n_out = (int)b->inst.size();
+  return SWCS_OK;
+}
+
+int swcs_batch_pool_size(swcs_batch* b, int i, int64_t* n_out) {
+  if (!b || !n_out || i < 0 || i >= (int)b->inst.size()) return bfail(b, SWCS_ERR_INVALID_ARG, "bad instance index");
+  *n_out = b->inst[i]->pool_size;
+  return SWCS_OK;
+}
+
+int swcs_batch_results(swcs_batch* b, int i, double* h_e, double* h_n2, double* h_g) {
+  if (!b || i < 0 || i >= (int)b->inst.size()) return bfail(b, SWCS_ERR_INVALID_ARG, "bad instance index");
+  int r = batch_check(b);
+  if (r) return r;
+  swcs_ctx* c = b->inst[i];
+  double out[2];
+  if (cudaMemcpy(out, ctrl(c)->eout, 16, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      (h_g && cudaMemcpy(h_g, c->gdev.p, sizeof(double) * c->pool_size, cudaMemcpyDeviceToHost) != cudaSuccess))
+    return bfail(b, SWCS_ERR_CUDA, "batch_results: copy failed");
+  if (h_e) *h_e = out[0];
+  if (h_n2) *h_n2 = out[1];
+  return SWCS_OK;
+}
+
+int swcs_batch_tuning(swcs_batch* b, double* h_out4) {
+  if (!b || !h_out4) return SWCS_ERR_INVALID_ARG;
+  h_out4[0] = b->share;
+  h_out4[1] = b->cluster;
+  h_out4[2] = b->tuned_ms;
+  h_out4[3] = (double)b->inst.size();
   return SWCS_OK;
 }
 

@@ -58,12 +58,85 @@ _SIGS = {
     "swcs_energy_noalloc": ([_vp, _vp, _vp, _i64, _vp], _i),
     "swcs_set_option": ([_vp, ctypes.c_char_p, _i64], _i),
     "swcs_sweep_energy": ([_vp, _pd, _pd], _i),
+    "swcs_batch_create": ([ctypes.POINTER(_vp), _vp], _i),
+    "swcs_batch_destroy": ([_vp], _i),
+    "swcs_batch_last_error": ([_vp], ctypes.c_char_p),
+    "swcs_batch_add": ([_vp, _vp, _vp, _i, _i, _vp, _vp, _i, _i64, ctypes.POINTER(_i)], _i),
+    "swcs_batch_build": ([_vp, _i], _i),
+    "swcs_batch_run": ([_vp], _i),
+    "swcs_batch_size": ([_vp, ctypes.POINTER(_i)], _i),
+    "swcs_batch_pool_size": ([_vp, _i, _p64], _i),
+    "swcs_batch_results": ([_vp, _i, _pd, _pd, _vp], _i),
+    "swcs_batch_tuning": ([_vp, _vp], _i),
 }
 
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(lib, _name)
     _f.argtypes = _args
     _f.restype = _res
+
+
+class Batch:
+    """Many independent instances evaluated by one graph launch (``swcs_batch``)."""
+
+    def __init__(self, stream=None):
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+            except Exception:
+                stream = 0
+        h = _vp()
+        r = lib.swcs_batch_create(ctypes.byref(h), _vp(stream))
+        if r != 0:
+            raise SwcsError(r, "swcs_batch_create failed")
+        self._h = h
+        self.pool_sizes = []
+
+    def _ck(self, r):
+        if r != 0:
+            raise SwcsError(r, lib.swcs_batch_last_error(self._h).decode())
+
+    def add(self, h, g, n_so, n_elec, ops, theta, n_keep):
+        h = _c(h, np.float64)
+        g = _c(g, np.float64)
+        ops = _c(ops, np.uint8).reshape(-1)
+        theta = _c(theta, np.float64)
+        idx = ctypes.c_int()
+        self._ck(lib.swcs_batch_add(self._h, _ptr(h), _ptr(g), int(n_so), int(n_elec), _ptr(ops), _ptr(theta),
+                                    len(theta), int(n_keep), ctypes.byref(idx)))
+        n = ctypes.c_int64()
+        self._ck(lib.swcs_batch_pool_size(self._h, idx.value, ctypes.byref(n)))
+        self.pool_sizes.append(n.value)
+        return idx.value
+
+    def build(self, autotune=True):
+        self._ck(lib.swcs_batch_build(self._h, 1 if autotune else 0))
+
+    def run(self):
+        self._ck(lib.swcs_batch_run(self._h))
+
+    def results(self, i):
+        e, n2 = ctypes.c_double(), ctypes.c_double()
+        g = np.zeros(self.pool_sizes[i])
+        self._ck(lib.swcs_batch_results(self._h, int(i), ctypes.byref(e), ctypes.byref(n2), _ptr(g)))
+        return e.value, n2.value, g
+
+    def tuning(self):
+        out = np.zeros(4)
+        self._ck(lib.swcs_batch_tuning(self._h, _ptr(out)))
+        return dict(share=out[0], cluster=int(out[1]), graph_ms=out[2], instances=int(out[3]))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.swcs_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def declared_symbols(header: str = HEADER):
