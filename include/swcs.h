@@ -106,8 +106,9 @@ int swcs_energy_dev(swcs_ctx* ctx, double* d_out);
 /* Pool gradient g_k = 2 <psi|H A_k|psi>/<psi|psi>, A_k = tau_k - tau_k^dag,
  * for the canonical pool (ADAPT step 4, Sec. II.C).  h_subset == NULL:
  * all pool entries are written to h_g_out[pool_size]; otherwise only
- * h_g_out[h_subset[i]] for i < n_subset (other entries untouched), and only
- * those operators' sigma contributions are formed. */
+ * h_g_out[h_subset[i]] for i < n_subset (other entries untouched).  With a
+ * subset the alpha-string row sweep skips the gradient contractions of every
+ * other operator (sigma itself is still formed in full). */
 int swcs_pool_gradients(swcs_ctx* ctx, double* h_g_out, const int64_t* h_subset, int64_t n_subset);
 int swcs_pool_gradients_dev(swcs_ctx* ctx, double* d_g_out, const int64_t* d_subset, int64_t n_subset);
 /* The pool sweep forms sigma on every determinant of the state as well, so it
@@ -181,6 +182,46 @@ int swcs_energy_noalloc(swcs_ctx* ctx, const uint64_t* d_keys, const double* d_a
  * clears them together with the swcs_stats counters. */
 int swcs_profile_enable(swcs_ctx* ctx, int on);
 int swcs_profile_read(swcs_ctx* ctx, double* h_ms8, int64_t* h_launches8, int reset);
+
+/* Learned pool screening.  The pool gradient of ADAPT step 4 is the dominant
+ * cost of the method (Sec. II.C; gradient evaluations take 43-57% of the
+ * time in Sec. III.D).  A small network predicts log10|g_k| from
+ * per-operator features so that only the predicted top fraction of the
+ * pool is evaluated exactly; the paper has no such network.
+ *   Network: 3 layers, width W (<= 256, multiple of 32), input d_in (multiple
+ *   of 32): H1 = bf16(relu(x W1^T + b1)), H2 = bf16(relu(H1 W2^T + b2)),
+ *   y = H2 . w3 + b3.  BF16 weights (rounded from FP32 master weights),
+ *   FP32 accumulation on the tensor cores.  Parameters, FP32, in the order
+ *   W1[W][d_in], b1[W], W2[W][W], b2[W], w3[W], b3.
+ *   x: BF16 bit patterns, [n][d_in] row-major, on the device.
+ *   swcs_mlp_grad_dev: gradients of the mean squared error to targets t[n]
+ *   into d_grad (parameter order; NULL to skip) and the loss into d_loss[0].
+ *   swcs_mlp_train_step_dev: the same gradients and one Adam step
+ *   (beta 0.9 / 0.999, eps 1e-8) of learning rate lr.
+ *   swcs_mlp_activations: H1, H2 (BF16 bits) and y of the last grad/train call.
+ *   swcs_pool_features_dev: SWCS_MLP_FEATURES features of every pool operator
+ *   for the context's current state, BF16 bits [pool_size][32].
+ *   swcs_pool_screen_dev: features, network, and the indices of the
+ *   ceil(frac * pool_size) largest predictions into d_subset (device,
+ *   pool_size capacity, unordered); *h_n_subset receives the count.
+ *   Feed them to swcs_pool_gradients_dev to evaluate only those operators.
+ *   swcs_log_abs_dev: t[i] = log10(|g[i]| + 1e-12) (training targets). */
+#define SWCS_MLP_FEATURES 32
+typedef struct swcs_mlp swcs_mlp;
+int swcs_mlp_create(swcs_mlp** out, void* cuda_stream, int d_in, int width);
+int swcs_mlp_destroy(swcs_mlp* m);
+const char* swcs_mlp_last_error(const swcs_mlp* m);
+int swcs_mlp_param_count(swcs_mlp* m, int64_t* n_out);
+int swcs_mlp_set_params(swcs_mlp* m, const float* h_params);
+int swcs_mlp_get_params(swcs_mlp* m, float* h_params);
+int swcs_mlp_forward_dev(swcs_mlp* m, const uint16_t* d_x, int64_t n, float* d_y);
+int swcs_mlp_grad_dev(swcs_mlp* m, const uint16_t* d_x, const float* d_t, int64_t n, float* d_grad, double* d_loss);
+int swcs_mlp_train_step_dev(swcs_mlp* m, const uint16_t* d_x, const float* d_t, int64_t n, float lr, double* d_loss);
+int swcs_mlp_activations(swcs_mlp* m, uint16_t* h_H1, uint16_t* h_H2, float* h_y, int64_t n);
+int swcs_mlp_sync(swcs_mlp* m);
+int swcs_log_abs_dev(const double* d_g, int64_t n, float* d_t, void* cuda_stream);
+int swcs_pool_features_dev(swcs_ctx* ctx, uint16_t* d_x);
+int swcs_pool_screen_dev(swcs_ctx* ctx, swcs_mlp* m, double frac, int64_t* d_subset, int64_t* h_n_subset);
 
 /* Batched launch: many independent instances (each its own Hamiltonian,
  * ansatz and N_keep) evaluated together -- ansatz, energy and full pool

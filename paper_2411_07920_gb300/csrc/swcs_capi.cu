@@ -38,7 +38,8 @@ struct swcs_ctx {
   double fci_dim = 0.0;
   int64_t pool_size = 0;
   std::vector<uint8_t> pool_ops;  // 5 bytes each
-  DevBuf h, J, Ws, G, opd, ops1, gstage;
+  DevBuf h, J, Ws, G, opd, ops1, gstage, pool_dev;
+  DevBuf selbits, feat, ypred, topk_hist, topk_ctl;
 
   // state
   DevBuf keys_a, amps_a, keys_b, amps_b, tab0, tab1;
@@ -436,7 +437,7 @@ __global__ void sincos_kernel(const double* th, double* cs, int n) {
 // Alpha-string row sweep; returns 1 when not applicable (caller falls back).
 // nd_bound >= 0: size buffers for that many determinants instead of reading
 // the state size (no host synchronisation); enqueue = false: only size.
-int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = true) {
+int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = true, const uint32_t* sel = nullptr) {
   const int m = c->n / 2;
   if (m > 32 || c->NB <= 0 || c->NB > (1 << 22)) return 1;
   const int64_t nd = nd_bound >= 0 ? nd_bound : host_state_size(c);
@@ -521,6 +522,7 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
   ra.max_ent_s = max_s;
   ra.max_ent_d = max_d;
   ra.touched_words = twords;
+  ra.sel_bits = sel;
   CK(launch_k(c, kKRow, [&] { return launch_row_sweep(ra, nthr, gsz, ncl, smem, c->st); }));
   c->stats[2] = 0;
   c->stats[3] = ncl;
@@ -530,9 +532,9 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
   return SWCS_OK;
 }
 
-int sweep(swcs_ctx* c, double* d_g) {
+int sweep(swcs_ctx* c, double* d_g, const uint32_t* sel = nullptr) {
   if (c->opt_sweep != 1) {
-    const int r = sweep_rows(c, d_g);
+    const int r = sweep_rows(c, d_g, -1, true, sel);
     if (r != 1) return r;
     if (c->opt_sweep == 2) return fail(c, SWCS_ERR_INVALID_ARG, "row sweep not applicable to this sector");
   }
@@ -661,7 +663,8 @@ int swcs_destroy(swcs_ctx* c) {
                     &c->gdev, &c->subset_dev, &c->gsub, &c->ext, &c->alpha_list, &c->rank_tab, &c->atab,
                     &c->gid_of, &c->gcount, &c->goff, &c->gfill, &c->gkey, &c->gamp, &c->grank, &c->rows,
                     &c->ck_keys, &c->ck_amps, &c->ck_n, &c->sn_keys, &c->sn_amps, &c->sn_n, &c->sigma, &c->nu0,
-                    &c->nu1, &c->atab0, &c->atab1, &c->dth};
+                    &c->nu1, &c->atab0, &c->atab1, &c->dth, &c->pool_dev, &c->selbits, &c->feat,
+                    &c->ypred, &c->topk_hist, &c->topk_ctl};
   for (DevBuf* b : bufs) release(*b);
   if (c->pin) cudaFreeHost(c->pin);
   for (auto& e : c->ev_pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
@@ -734,6 +737,8 @@ int swcs_load_hamiltonian(swcs_ctx* c, const double* h_h, const double* h_g, int
     CK(cudaMemcpyAsync(c->rank_tab.p, T.data(), T.size() * 4, cudaMemcpyHostToDevice, c->st));
   }
   CK(cudaMemcpyAsync(c->opd.p, opd.data(), np2 * 4, cudaMemcpyHostToDevice, c->st));
+  if ((r = ensure(c, c->pool_dev, c->pool_ops.size() + 16))) return r;
+  CK(cudaMemcpyAsync(c->pool_dev.p, c->pool_ops.data(), c->pool_ops.size(), cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(c->ops1.p, ops1.data(), n2 * 4, cudaMemcpyHostToDevice, c->st));
   CK(cudaStreamSynchronize(c->st));
   c->have_ham = true;
@@ -844,11 +849,15 @@ int swcs_pool_gradients_dev(swcs_ctx* c, double* d_g_out, const int64_t* d_subse
   if (r) return r;
   if (!d_g_out) return fail(c, SWCS_ERR_INVALID_ARG, "null output");
   double* g = d_g_out;
+  const uint32_t* sel = nullptr;
   if (d_subset) {
     if ((r = ensure(c, c->gdev, sizeof(double) * c->pool_size))) return r;
     g = (double*)c->gdev.p;
+    if ((r = ensure(c, c->selbits, ((c->pool_size + 31) / 32) * 4 + 4))) return r;
+    CK(launch_k(c, kKOther, [&] { return launch_subset_bits(d_subset, n_subset, (uint32_t*)c->selbits.p, c->pool_size, c->st); }));
+    sel = (const uint32_t*)c->selbits.p;
   }
-  if ((r = sweep(c, g))) return r;
+  if ((r = sweep(c, g, sel))) return r;
   if (d_subset) CK(launch_k(c, kKOther, [&] { return launch_gather_subset(g, d_subset, n_subset, d_g_out, c->st); }));
   return SWCS_OK;
 }
@@ -969,6 +978,37 @@ int swcs_sweep_energy(swcs_ctx* c, double* e_out, double* n2_out) {
   if ((r = check_device(c, "swcs_sweep_energy"))) return r;
   if (e_out) *e_out = out[0];
   if (n2_out) *n2_out = out[1];
+  return SWCS_OK;
+}
+
+int swcs_pool_features_dev(swcs_ctx* c, uint16_t* d_x) {
+  int r = need_state(c);
+  if (r) return r;
+  if (!d_x) return fail(c, SWCS_ERR_INVALID_ARG, "null output");
+  CK(launch_k(c, kKOther, [&] {
+    return launch_pool_features(ham_dev(c), state_dev(c), (const uint8_t*)c->pool_dev.p, c->pool_size, (__nv_bfloat16*)d_x, c->st);
+  }));
+  return SWCS_OK;
+}
+
+int swcs_pool_screen_dev(swcs_ctx* c, swcs_mlp* m, double frac, int64_t* d_subset, int64_t* h_n_subset) {
+  int r = need_state(c);
+  if (r) return r;
+  if (!m || !d_subset || !(frac > 0.0) || frac > 1.0) return fail(c, SWCS_ERR_INVALID_ARG, "bad screening arguments");
+  const int64_t P = c->pool_size;
+  const int64_t k = std::max<int64_t>(1, (int64_t)std::ceil(frac * (double)P));
+  if ((r = ensure(c, c->feat, (size_t)P * kFeatures * 2)) || (r = ensure(c, c->ypred, (size_t)P * 4)) ||
+      (r = ensure(c, c->topk_hist, 2 * 65536 * 4)) || (r = ensure(c, c->topk_ctl, 8 * 8)))
+    return r;
+  if ((r = swcs_pool_features_dev(c, (uint16_t*)c->feat.p))) return r;
+  if ((r = swcs_mlp_forward_dev(m, (const uint16_t*)c->feat.p, P, (float*)c->ypred.p)))
+    return fail(c, r, "screening network: %s", swcs_mlp_last_error(m));
+  CK(launch_k(c, kKOther, [&] {
+    return launch_topk((const float*)c->ypred.p, P, k, (unsigned*)c->topk_hist.p, (unsigned long long*)c->topk_ctl.p,
+                       d_subset, c->st);
+  }));
+  c->launches += 4;
+  if (h_n_subset) *h_n_subset = k;
   return SWCS_OK;
 }
 

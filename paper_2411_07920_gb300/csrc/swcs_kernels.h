@@ -3,6 +3,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <cuda_bf16.h>
+
 #include "swcs_device.cuh"
 
 namespace swcs {
@@ -118,6 +120,7 @@ struct RowArgs {
   int* err;
   int max_ent_s, max_ent_d;
   int touched_words;  // words of the per-CTA touched-entry bitmap (0: clear whole rows)
+  const uint32_t* sel_bits;  // pool operators to evaluate (nullptr: all)
 };
 
 struct GroupArgs {
@@ -164,6 +167,53 @@ struct AdjArgs {
 };
 cudaError_t launch_adjoint_gate(const AdjArgs& a, int nblocks, cudaStream_t st);
 cudaError_t launch_scale_dtheta(double* d, int n, const double* acc, cudaStream_t st);
+
+// Screening network (swcs_mlp.cu).
+enum GemmMode { kGemmF32 = 0, kGemmReluBf16 = 1, kGemmReluBf16Dot = 2 };
+struct GemmArgs {
+  const __nv_bfloat16* A;  // [M x K], row stride lda (elements), K contiguous
+  const __nv_bfloat16* B;  // [N x K], row stride ldb
+  int lda, ldb;
+  int M, N, K;             // N in [16, 256], N % 16 == 0, K % 32 == 0
+  int mode;
+  const float* bias;       // [N] (ReLU modes)
+  float* out_f32;          // kGemmF32: [M x N], row stride ldo
+  __nv_bfloat16* out_bf16; // ReLU modes: [M x N], row stride ldo
+  int ldo;
+  const __nv_bfloat16* w3; // kGemmReluBf16Dot: y[row] = sum_j out[row][j] w3[j] + b3
+  float b3;
+  float* y;
+  int* err;
+};
+struct MlpParams {
+  float* master;
+  float* m;
+  float* v;
+  int n_params, d_in, width;
+  int off_W1, off_b1, off_W2, off_b2, off_w3, off_b3;
+  __nv_bfloat16* W1b;
+  __nv_bfloat16* W2b;
+  __nv_bfloat16* W2tb;
+  __nv_bfloat16* w3b;
+};
+cudaError_t launch_mlp_gemm(const GemmArgs& g, cudaStream_t st);
+cudaError_t launch_mlp_dy(const float* y, const float* t, int B, float* dy, double* loss, cudaStream_t st);
+cudaError_t launch_mlp_dz2(const float* dy, const __nv_bfloat16* w3, const __nv_bfloat16* H2, int B, int W,
+                           __nv_bfloat16* dZ2, float* dw3, float* db3, cudaStream_t st);
+cudaError_t launch_mlp_dz1(const float* dH1, const __nv_bfloat16* H1, size_t n, __nv_bfloat16* dZ1, cudaStream_t st);
+cudaError_t launch_mlp_colsum(const __nv_bfloat16* Z, int B, int W, float* db, cudaStream_t st);
+cudaError_t launch_mlp_transpose(const __nv_bfloat16* in, int R, int C, int Rpad, __nv_bfloat16* out, cudaStream_t st);
+cudaError_t launch_mlp_adam(const MlpParams& p, const float* grad, float lr, int step, cudaStream_t st);
+cudaError_t launch_mlp_refresh(const MlpParams& p, cudaStream_t st);
+
+// Pool features and top-k selection (swcs_screen.cu).
+constexpr int kFeatures = 32;
+cudaError_t launch_pool_features(const HamDev& H, const StateDev& S, const uint8_t* pool_ops, int64_t n_pool,
+                                 __nv_bfloat16* x, cudaStream_t st);
+cudaError_t launch_topk(const float* y, int64_t n, int64_t k, unsigned* hist, unsigned long long* ctl,
+                        int64_t* out_idx, cudaStream_t st);
+cudaError_t launch_subset_bits(const int64_t* subset, int64_t n, uint32_t* bits, int64_t n_pool, cudaStream_t st);
+cudaError_t launch_log_abs(const double* g, int64_t n, float* t, cudaStream_t st);
 
 // Hamiltonian preparation from the full <pq||rs> array on the device.
 cudaError_t launch_pack_hamiltonian(const double* g_full, int n, double* J, double* Ws, double* G,

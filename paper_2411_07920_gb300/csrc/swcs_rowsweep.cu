@@ -106,25 +106,29 @@ __device__ __forceinline__ void row_pair(const RowArgs& A, double* row, unsigned
                                          uint32_t rank_e, int p, int q, int r, int s, const uint8_t* occ_all) {
   const int n = A.H.n;
   if (q < 0) {
-    const int sb = single_phase(d, p, r);
     if (SCATTER) {
+      const int sb = single_phase(d, p, r);
       atomicAdd(&row[rank_e], apply_sign(fock_single(A, occ_all, p, r), sb) * cd);
       mark(touched, rank_e);
     } else {
       const int lo = p < r ? p : r, hi = p < r ? r : p;
       const int k = A.H.ops1[lo * n + hi];
+      if (A.sel_bits && !((__ldg(&A.sel_bits[k >> 5]) >> (k & 31)) & 1u)) return;
+      const int sb = single_phase(d, p, r);
       atomicAdd(&A.g[k], apply_sign(cd * row[rank_e], sb ^ (int)(p > r)));
     }
     return;
   }
-  const int sb = double_phase(d, p, q, r, s);
   const int pa = pair_index(p, q, n), pb = pair_index(r, s, n);
   if (SCATTER) {
+    const int sb = double_phase(d, p, q, r, s);
     atomicAdd(&row[rank_e], apply_sign(A.H.G[(size_t)pa * A.H.npairs + pb], sb) * cd);
     mark(touched, rank_e);
   } else {
     const bool down = pa > pb;
     const int k = down ? A.H.opd[(size_t)pb * A.H.npairs + pa] : A.H.opd[(size_t)pa * A.H.npairs + pb];
+    if (A.sel_bits && !((__ldg(&A.sel_bits[k >> 5]) >> (k & 31)) & 1u)) return;
+    const int sb = double_phase(d, p, q, r, s);
     atomicAdd(&A.g[k], apply_sign(cd * row[rank_e], sb ^ (int)down));
   }
 }

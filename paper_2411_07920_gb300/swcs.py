@@ -68,6 +68,20 @@ _SIGS = {
     "swcs_batch_pool_size": ([_vp, _i, _p64], _i),
     "swcs_batch_results": ([_vp, _i, _pd, _pd, _vp], _i),
     "swcs_batch_tuning": ([_vp, _vp], _i),
+    "swcs_mlp_create": ([ctypes.POINTER(_vp), _vp, _i, _i], _i),
+    "swcs_mlp_destroy": ([_vp], _i),
+    "swcs_mlp_last_error": ([_vp], ctypes.c_char_p),
+    "swcs_mlp_param_count": ([_vp, _p64], _i),
+    "swcs_mlp_set_params": ([_vp, _vp], _i),
+    "swcs_mlp_get_params": ([_vp, _vp], _i),
+    "swcs_mlp_forward_dev": ([_vp, _vp, _i64, _vp], _i),
+    "swcs_mlp_grad_dev": ([_vp, _vp, _vp, _i64, _vp, _vp], _i),
+    "swcs_mlp_train_step_dev": ([_vp, _vp, _vp, _i64, ctypes.c_float, _vp], _i),
+    "swcs_mlp_activations": ([_vp, _vp, _vp, _vp, _i64], _i),
+    "swcs_mlp_sync": ([_vp], _i),
+    "swcs_log_abs_dev": ([_vp, _i64, _vp, _vp], _i),
+    "swcs_pool_features_dev": ([_vp, _vp], _i),
+    "swcs_pool_screen_dev": ([_vp, _vp, ctypes.c_double, _vp, _p64], _i),
 }
 
 for _name, (_args, _res) in _SIGS.items():
@@ -137,6 +151,91 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Mlp:
+    """Screening network (``swcs_mlp``); tensors are torch CUDA tensors."""
+
+    def __init__(self, d_in=32, width=256, stream=None):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        h = _vp()
+        r = lib.swcs_mlp_create(ctypes.byref(h), _vp(stream), int(d_in), int(width))
+        if r != 0:
+            raise SwcsError(r, "swcs_mlp_create failed")
+        self._h = h
+        self.d_in, self.width = d_in, width
+        n = ctypes.c_int64()
+        lib.swcs_mlp_param_count(h, ctypes.byref(n))
+        self.n_params = n.value
+        self._stream = stream
+
+    def _ck(self, r):
+        if r != 0:
+            raise SwcsError(r, lib.swcs_mlp_last_error(self._h).decode())
+
+    def layout(self):
+        W, D = self.width, self.d_in
+        o = {}
+        o["W1"] = (0, (W, D))
+        o["b1"] = (W * D, (W,))
+        o["W2"] = (W * D + W, (W, W))
+        o["b2"] = (W * D + W + W * W, (W,))
+        o["w3"] = (W * D + 2 * W + W * W, (W,))
+        o["b3"] = (W * D + 3 * W + W * W, ())
+        return o
+
+    def set_params(self, flat):
+        flat = _c(flat, np.float32)
+        assert flat.size == self.n_params
+        self._ck(lib.swcs_mlp_set_params(self._h, _ptr(flat)))
+
+    def get_params(self):
+        out = np.zeros(self.n_params, np.float32)
+        self._ck(lib.swcs_mlp_get_params(self._h, _ptr(out)))
+        return out
+
+    def forward_dev(self, d_x, d_y):
+        self._ck(lib.swcs_mlp_forward_dev(self._h, _tptr(d_x), int(d_x.shape[0]), _tptr(d_y)))
+
+    def grad_dev(self, d_x, d_t, d_grad, d_loss):
+        self._ck(lib.swcs_mlp_grad_dev(self._h, _tptr(d_x), _tptr(d_t), int(d_x.shape[0]), _tptr(d_grad),
+                                       _tptr(d_loss)))
+
+    def train_step_dev(self, d_x, d_t, lr, d_loss):
+        self._ck(lib.swcs_mlp_train_step_dev(self._h, _tptr(d_x), _tptr(d_t), int(d_x.shape[0]), float(lr),
+                                             _tptr(d_loss)))
+
+    def activations(self, n):
+        H1 = np.zeros((n, self.width), np.uint16)
+        H2 = np.zeros((n, self.width), np.uint16)
+        y = np.zeros(n, np.float32)
+        self._ck(lib.swcs_mlp_activations(self._h, _ptr(H1), _ptr(H2), _ptr(y), int(n)))
+        return H1, H2, y
+
+    def sync(self):
+        self._ck(lib.swcs_mlp_sync(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.swcs_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def log_abs_dev(d_g, d_t, stream=None):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    r = lib.swcs_log_abs_dev(_tptr(d_g), int(d_g.numel()), _tptr(d_t), _vp(stream))
+    if r != 0:
+        raise SwcsError(r, "swcs_log_abs_dev failed")
 
 
 def declared_symbols(header: str = HEADER):
@@ -287,6 +386,14 @@ class Context:
         e, n2 = ctypes.c_double(), ctypes.c_double()
         self._ck(lib.swcs_sweep_energy(self._h, ctypes.byref(e), ctypes.byref(n2)))
         return e.value, n2.value
+
+    def pool_features_dev(self, d_x):
+        self._ck(lib.swcs_pool_features_dev(self._h, _tptr(d_x)))
+
+    def pool_screen_dev(self, mlp, frac, d_subset):
+        n = ctypes.c_int64()
+        self._ck(lib.swcs_pool_screen_dev(self._h, mlp._h, float(frac), _tptr(d_subset), ctypes.byref(n)))
+        return n.value
 
     def set_option(self, name, value):
         self._ck(lib.swcs_set_option(self._h, name.encode(), int(value)))
