@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--threads", type=int, default=512, help="threads per CTA of the row sweep")
     p.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched leg")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
+    p.add_argument("--no-screen", action="store_true", help="skip the learned-screening leg")
     return p.parse_args()
 
 
@@ -317,6 +318,11 @@ def run_swcs(args):
         adjoint = {"ms": round(1e3 * min(ts[1:]), 3), "params": int(len(w.theta)), "ckpt_every": 20,
                    "energy": e_adj, "grad_norm": float(np.linalg.norm(d_adj))}
 
+    # ------------------------------------------------------------ learned screening leg (same state)
+    screen_res = None
+    if not args.no_screen:
+        screen_res = run_screen_leg(swcs, ctx, w, args, torch)
+
     # ------------------------------------------------------------ batched leg: 64 uneven instances
     batch = None
     if not args.no_batch:
@@ -340,7 +346,7 @@ def run_swcs(args):
                            "parallelism": f"replicas x{world}", "l2": "flushed between steps (512 MB write)"},
                 "gate_dets_per_s": gate_dets_per_s, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "energy_ms": round(min(energy_ms), 3),
-                "adjoint": adjoint, "batch": batch,
+                "adjoint": adjoint, "batch": batch, "screen": screen_res,
                 "kernels_ms": {k: round(v[0], 3) for k, v in prof.items()},
                 "ext": {"distinct": stats["ext_distinct"], "buckets": stats["ext_buckets"],
                         "capacity": stats["ext_capacity"]}}
@@ -348,6 +354,57 @@ def run_swcs(args):
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_screen_leg(swcs, ctx, w, args, torch, frac=0.05):
+    """Train the screening network on exact pool gradients of the small
+    workload families (12/4 untruncated, 20/6 and 28/8 truncated), then screen
+    the 52/12 state: features, network, top 5%, subset sweep -- against the
+    full sweep of the same state.  Also times the network's forward pass over
+    the whole pool (tensor-core GEMMs)."""
+    from paper_2411_07920_gb300 import screen
+    t0 = time.perf_counter()
+    X, T = screen.training_set(screen.default_specs())
+    net = swcs.Mlp(32, 256)
+    net.set_params(screen.init_params(seed=0))
+    hist = screen.train(net, X, T)
+    t_train = time.perf_counter() - t0
+    ctx.apply_ansatz(w.ops, w.theta, args.n_keep)
+    res = []
+    for _ in range(3):
+        res.append(screen.evaluate(ctx, net, frac))
+    best = min(res, key=lambda r: r["t_screened"])
+    best["t_full"] = min(r["t_full"] for r in res)
+    best["speedup"] = best["t_full"] / best["t_screened"]
+    # network forward over the whole pool, device time
+    P = ctx.pool_size()
+    x = torch.empty((P, 32), dtype=torch.int16, device="cuda")
+    ctx.pool_features_dev(x)
+    y = torch.empty(P, dtype=torch.float32, device="cuda")
+    net.forward_dev(x, y)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(10):
+        net.forward_dev(x, y)
+    e1.record(st)
+    e1.synchronize()
+    t_fwd = e0.elapsed_time(e1) / 10 / 1e3
+    flops = 2.0 * P * (32 * 256 + 256 * 256 + 256)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    net.close()
+    return {"frac": frac, "subset": best["subset"], "pool": best["pool"], "recall_argmax": best["recall_argmax"],
+            "recall_top10": best["recall_top10"], "same_argmax": bool(best["same_argmax"]),
+            "max_abs_err_on_subset": best["max_abs_err_on_subset"], "full_ms": round(1e3 * best["t_full"], 3),
+            "screened_ms": round(1e3 * best["t_screened"], 3), "speedup": round(best["speedup"], 3),
+            "train_s": round(t_train, 2), "train_samples": int(X.shape[0]), "train_loss": hist[-1][1],
+            "mlp_forward": {"ms": round(1e3 * t_fwd, 4), "tflops": round(flops / t_fwd / 1e12, 2),
+                            "frac_of_bf16_peak": round(flops / t_fwd / 1e12 / bf16_peak, 4)}}
 
 
 def run_batch_leg(swcs, I, torch, n_inst=64, seed0=100, reps=3):

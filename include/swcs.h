@@ -205,7 +205,7 @@ int swcs_profile_read(swcs_ctx* ctx, double* h_ms8, int64_t* h_launches8, int re
  *   ceil(frac * pool_size) largest predictions into d_subset (device,
  *   pool_size capacity, unordered); *h_n_subset receives the count.
  *   Feed them to swcs_pool_gradients_dev to evaluate only those operators.
- *   swcs_log_abs_dev: t[i] = log10(|g[i]| + 1e-12) (training targets). */
+ *   swcs_log_abs_dev: t[i] = max(log10(|g[i]| + 1e-12), -10) (training targets). */
 #define SWCS_MLP_FEATURES 32
 typedef struct swcs_mlp swcs_mlp;
 int swcs_mlp_create(swcs_mlp** out, void* cuda_stream, int d_in, int width);

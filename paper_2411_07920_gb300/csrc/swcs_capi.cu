@@ -39,7 +39,7 @@ struct swcs_ctx {
   int64_t pool_size = 0;
   std::vector<uint8_t> pool_ops;  // 5 bytes each
   DevBuf h, J, Ws, G, opd, ops1, gstage, pool_dev;
-  DevBuf selbits, feat, ypred, topk_hist, topk_ctl;
+  DevBuf selbits, feat, ypred, topk_hist, topk_ctl, occ;
 
   // state
   DevBuf keys_a, amps_a, keys_b, amps_b, tab0, tab1;
@@ -664,7 +664,7 @@ int swcs_destroy(swcs_ctx* c) {
                     &c->gid_of, &c->gcount, &c->goff, &c->gfill, &c->gkey, &c->gamp, &c->grank, &c->rows,
                     &c->ck_keys, &c->ck_amps, &c->ck_n, &c->sn_keys, &c->sn_amps, &c->sn_n, &c->sigma, &c->nu0,
                     &c->nu1, &c->atab0, &c->atab1, &c->dth, &c->pool_dev, &c->selbits, &c->feat,
-                    &c->ypred, &c->topk_hist, &c->topk_ctl};
+                    &c->ypred, &c->topk_hist, &c->topk_ctl, &c->occ};
   for (DevBuf* b : bufs) release(*b);
   if (c->pin) cudaFreeHost(c->pin);
   for (auto& e : c->ev_pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
@@ -985,9 +985,12 @@ int swcs_pool_features_dev(swcs_ctx* c, uint16_t* d_x) {
   int r = need_state(c);
   if (r) return r;
   if (!d_x) return fail(c, SWCS_ERR_INVALID_ARG, "null output");
+  if ((r = ensure(c, c->occ, 64 * sizeof(double)))) return r;
   CK(launch_k(c, kKOther, [&] {
-    return launch_pool_features(ham_dev(c), state_dev(c), (const uint8_t*)c->pool_dev.p, c->pool_size, (__nv_bfloat16*)d_x, c->st);
+    return launch_pool_features(ham_dev(c), state_dev(c), (const uint8_t*)c->pool_dev.p, c->pool_size, (double*)c->occ.p,
+                                (__nv_bfloat16*)d_x, c->st);
   }));
+  c->launches += 1;
   return SWCS_OK;
 }
 

@@ -209,7 +209,7 @@ cudaError_t launch_mlp_refresh(const MlpParams& p, cudaStream_t st);
 // Pool features and top-k selection (swcs_screen.cu).
 constexpr int kFeatures = 32;
 cudaError_t launch_pool_features(const HamDev& H, const StateDev& S, const uint8_t* pool_ops, int64_t n_pool,
-                                 __nv_bfloat16* x, cudaStream_t st);
+                                 double* occ, __nv_bfloat16* x, cudaStream_t st);
 cudaError_t launch_topk(const float* y, int64_t n, int64_t k, unsigned* hist, unsigned long long* ctl,
                         int64_t* out_idx, cudaStream_t st);
 cudaError_t launch_subset_bits(const int64_t* subset, int64_t n, uint32_t* bits, int64_t n_pool, cudaStream_t st);

@@ -3,14 +3,16 @@
 // pool, Sec. II.C: only the selected operators' gradients are then formed).
 //
 // Features of operator k (tau_k removes (p,q) and adds (r,s); singles p -> r),
-// all independent of the system size:
+// all independent of the system size; L(x) = log10(|x| + 1e-12) / 4:
 //   0 double?  1-4 indices / n_so  5-8 h_pp, h_qq, h_rr, h_ss  9 orbital-energy gap
-//   10 log10|<rs||pq>| (singles: log10|Fock_rp| on the reference)  11 log10(|v| / max(|gap|, 0.1))
+//   10 L(<rs||pq>) (singles: Fock_rp on the reference)  11 L(v / max(|gap|, 0.1))
 //   12 occupied-in-reference count of (p,q) / 2   13 of (r,s) / 2
-//   14 log10|c_ref|   15 log10|c(tau_k ref)|   16 log10|c(tau_k^dag ref)|
-//   17 opposite-spin pair?  18 same-spin double?  19 1/(1+|gap|)
-//   20 log10|2 c_ref v|  21 zero  22 n_e/n_so  23 n_so/64  24-31 zero
-// (log10 of zero is floored at -12).
+//   14 L(c_ref)   15 L(c(tau_k ref))   16 L(c(tau_k^dag ref))
+//   17 opposite-spin pair?  18 same-spin double?  19 1/(1+|gap|)  20 L(2 c_ref v)
+//   21 L(n_p n_q (1-n_r)(1-n_s)): weight of determinants tau_k acts on, from the
+//      state's orbital occupations n_p = <psi|a+_p a_p|psi>/<psi|psi>
+//   22 n_e/n_so  23 n_so/64  24 L(n_r n_s (1-n_p)(1-n_q))  25-28 n_p, n_q, n_r, n_s
+//   29 L(v (w_up + w_dn))  30-31 zero
 #include <algorithm>
 #include <cstdint>
 #include <cuda_bf16.h>
@@ -23,15 +25,42 @@ namespace swcs {
 
 namespace {
 
-__device__ __forceinline__ float lg(double v) { return (float)log10(fabs(v) + 1e-12); }
+__device__ __forceinline__ float lg(double v) { return (float)(0.25 * log10(fabs(v) + 1e-12)); }
 
 __device__ __forceinline__ double amp_of(const StateDev& S, uint64_t key) {
   const int64_t j = idx_lookup(S.tab, S.tab_mask, key);
   return j >= 0 ? S.amps[j] : 0.0;
 }
 
-__global__ void features_kernel(HamDev H, StateDev S, const uint8_t* pool_ops, int64_t n_pool, __nv_bfloat16* x) {
+// occ[p] += sum_D c_D^2 [p in D]
+__global__ void occupation_kernel(StateDev S, double* occ) {
+  __shared__ double acc[64];
+  for (int t = threadIdx.x; t < 64; t += blockDim.x) acc[t] = 0.0;
+  __syncthreads();
+  const long long n = *S.n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    uint64_t d = S.keys[i];
+    const double w = S.amps[i] * S.amps[i];
+    while (d) {
+      const int p = __ffsll((long long)d) - 1;
+      d &= d - 1;
+      atomicAdd(&acc[p], w);
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 64; t += blockDim.x)
+    if (acc[t] != 0.0) atomicAdd(&occ[t], acc[t]);
+}
+
+__global__ void features_kernel(HamDev H, StateDev S, const uint8_t* pool_ops, int64_t n_pool, const double* occ,
+                                __nv_bfloat16* x) {
+  __shared__ double nocc[64];
   const int n = H.n;
+  double tot = 0.0;
+  for (int t = 0; t < n; ++t) tot += occ[t];
+  const double n2 = tot / H.ne;
+  for (int t = threadIdx.x; t < 64; t += blockDim.x) nocc[t] = t < n ? occ[t] / n2 : 0.0;
+  __syncthreads();
   const uint64_t ref = (H.ne >= 64) ? ~0ull : ((1ull << H.ne) - 1ull);
   const double c_ref = amp_of(S, ref);
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_pool; k += (int64_t)gridDim.x * blockDim.x) {
@@ -69,6 +98,8 @@ __global__ void features_kernel(HamDev H, StateDev S, const uint8_t* pool_ops, i
     f[7] = (float)er;
     f[8] = (float)es;
     f[9] = (float)gap;
+    const double np_ = nocc[p], nq = dbl ? nocc[q] : 1.0, nr = nocc[r], ns = dbl ? nocc[s] : 0.0;
+    const double w_up = np_ * nq * (1.0 - nr) * (1.0 - ns), w_dn = nr * (dbl ? ns : 1.0) * (1.0 - np_) * (dbl ? 1.0 - nq : 1.0);
     f[10] = lg(v);
     f[11] = lg(fabs(v) / fmax(fabs(gap), 0.1));
     f[12] = 0.5f * occ_lo;
@@ -80,6 +111,13 @@ __global__ void features_kernel(HamDev H, StateDev S, const uint8_t* pool_ops, i
     f[18] = (dbl && ((p & 1) == (q & 1))) ? 1.f : 0.f;
     f[19] = (float)(1.0 / (1.0 + fabs(gap)));
     f[20] = lg(2.0 * c_ref * v);
+    f[21] = lg(w_up);
+    f[24] = lg(w_dn);
+    f[25] = (float)np_;
+    f[26] = (float)(dbl ? nq : np_);
+    f[27] = (float)nr;
+    f[28] = (float)(dbl ? ns : nr);
+    f[29] = lg(fabs(v) * (w_up + w_dn));
     f[22] = (float)H.ne / n;
     f[23] = (float)n / 64.f;
     __nv_bfloat16* row = x + (size_t)k * kFeatures;
@@ -161,14 +199,17 @@ __global__ void subset_bits_kernel(const int64_t* subset, int64_t n, uint32_t* b
 
 __global__ void log_abs_kernel(const double* g, int64_t n, float* t) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    t[i] = (float)log10(fabs(g[i]) + 1e-12);
+    t[i] = (float)fmax(log10(fabs(g[i]) + 1e-12), -10.0);
 }
 
 }  // namespace
 
 cudaError_t launch_pool_features(const HamDev& H, const StateDev& S, const uint8_t* pool_ops, int64_t n_pool,
-                                 __nv_bfloat16* x, cudaStream_t st) {
-  features_kernel<<<(int)((n_pool + 255) / 256), 256, 0, st>>>(H, S, pool_ops, n_pool, x);
+                                 double* occ, __nv_bfloat16* x, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(occ, 0, 64 * sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  occupation_kernel<<<304, 256, 0, st>>>(S, occ);
+  features_kernel<<<(int)((n_pool + 255) / 256), 256, 0, st>>>(H, S, pool_ops, n_pool, occ, x);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,71 @@
+"""Learned screening: the subset sweep is exact on its subset, and the trained
+network's top fraction recalls the exact argmax far above chance."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2411_07920_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2411_07920_gb300 import swcs
+    return swcs
+
+
+def test_subset_sweep_is_exact_on_its_subset(S):
+    import torch
+    w = I.small_case(20, 6, 45, 303, n_keep=500)
+    c = S.Context()
+    c.load_hamiltonian(w.h, w.g, w.n_so, w.n_e)
+    c.apply_ansatz(w.ops, w.theta, 500)
+    ko, ao = O.apply_ansatz(w.n_so, w.n_e, w.ops, w.theta, 500)
+    go = O.pool_gradients(w.n_so, w.h, w.g, ko, ao)
+    P = c.pool_size()
+    rng = np.random.default_rng(1)
+    sub = np.sort(rng.choice(P, P // 20, replace=False)).astype(np.int64)
+    d_sub = torch.from_numpy(sub).cuda()
+    d_g = torch.full((P,), float("nan"), dtype=torch.float64, device="cuda")
+    c.pool_gradients_dev(d_g, d_sub)
+    g = d_g.cpu().numpy()
+    assert np.abs(g[sub] - go[sub]).max() < TOL
+    assert np.isnan(np.delete(g, sub)).all()
+    # the features are finite and deterministic
+    x1 = torch.empty((P, 32), dtype=torch.int16, device="cuda")
+    x2 = torch.empty((P, 32), dtype=torch.int16, device="cuda")
+    c.pool_features_dev(x1)
+    c.pool_features_dev(x2)
+    assert torch.equal(x1, x2)
+    c.close()
+
+
+def test_trained_screen_recalls_argmax(S):
+    from paper_2411_07920_gb300 import screen
+    specs = [(12, 4, 10, s, 0) for s in (1, 11, 21)] + [(20, 6, 40, s, 2000) for s in (5, 15)] + \
+            [(24, 8, 40, s, 4000) for s in (6, 16)]
+    X, T = screen.training_set(specs)
+    net = S.Mlp(32, 256)
+    net.set_params(screen.init_params(seed=0))
+    hist = screen.train(net, X, T, steps=800, batch=8192, lr=3e-3)
+    print("training loss", hist)
+    assert hist[-1][1] < 0.5 * hist[0][1]
+    recalls, top10 = [], []
+    for (n_so, n_e, n_ops, sd, nk) in [(24, 8, 50, 401, 3000), (24, 8, 50, 402, 3000), (28, 8, 60, 403, 5000),
+                                      (20, 6, 40, 404, 1500)]:
+        w = I.small_case(n_so, n_e, n_ops, sd, n_keep=nk)
+        c = S.Context()
+        c.load_hamiltonian(w.h, w.g, w.n_so, w.n_e)
+        c.apply_ansatz(w.ops, w.theta, nk)
+        r = screen.evaluate(c, net, frac=0.05)
+        assert r["max_abs_err_on_subset"] < TOL
+        recalls.append(r["recall_argmax"])
+        top10.append(r["recall_top10"])
+        c.close()
+    print("screen recall argmax", recalls, "top10", top10)
+    # a random 5% subset holds the argmax with probability 0.05
+    assert np.mean(recalls) >= 0.75
+    assert np.mean(top10) >= 0.5
+    net.close()
