@@ -129,6 +129,10 @@ int swcs_energy_grad(swcs_ctx* ctx, const uint8_t* h_ops, const double* h_theta,
 int swcs_state_size(swcs_ctx* ctx, int64_t* n_out);
 int swcs_get_state(swcs_ctx* ctx, uint64_t* h_keys, double* h_amps, int64_t cap, int64_t* n_out);
 int swcs_set_state(swcs_ctx* ctx, const uint64_t* h_keys, const double* h_amps, int64_t n);
+/* sigma_D = (H psi)_D for every determinant D of the current state (the
+ * vector the energy kernel forms), with the bitstrings, sorted by bitstring;
+ * same size/cap convention as swcs_get_state. */
+int swcs_get_sigma(swcs_ctx* ctx, uint64_t* h_keys, double* h_sigma, int64_t cap, int64_t* n_out);
 
 /* Diagnostics accumulated since the last swcs_profile_read(.., reset=1):
  * {gates applied, radix-select passes, distinct determinants in the last

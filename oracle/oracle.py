@@ -59,6 +59,10 @@ def _load():
     L.orc_energy_grad.argtypes = [c_int, c_int, _f64p, _f64p, _u8p, _f64p, c_int, c_i64,
                                   ctypes.POINTER(c_d), _f64p]
     L.orc_energy_grad.restype = None
+    L.orc_sigma_at.argtypes = [c_int, _f64p, _f64p, _u64p, _f64p, c_i64, _u64p, c_i64, _f64p]
+    L.orc_sigma_at.restype = None
+    L.orc_pool_gradients_pull.argtypes = [c_int, _f64p, _f64p, _u64p, _f64p, c_i64, _i64p, c_i64, _f64p]
+    L.orc_pool_gradients_pull.restype = None
     _lib = L
     return L
 
@@ -171,3 +175,23 @@ def energy_grad(n_so, n_e, h, g, ops, theta, n_keep):
     L.orc_energy_grad(n_so, n_e, hh, gg, _c(ops, np.uint8).reshape(-1), theta, len(theta), int(n_keep),
                       ctypes.byref(e), d)
     return e.value, d
+
+
+def sigma_at(n_so, h, g, keys, amps, at):
+    """sigma_E = (H psi)_E at the given determinants, each pulled on its own."""
+    L = _load()
+    hh, gg = _ham(h, g)
+    at = _c(at, np.uint64)
+    out = np.zeros(len(at))
+    L.orc_sigma_at(n_so, hh, gg, _c(keys, np.uint64), _c(amps, np.float64), len(keys), at, len(at), out)
+    return out
+
+
+def pool_gradients_pull(n_so, h, g, keys, amps, subset):
+    """Pool gradient of the listed operators, sigma pulled per needed determinant."""
+    L = _load()
+    hh, gg = _ham(h, g)
+    sub = _c(subset, np.int64)
+    out = np.zeros(len(sub))
+    L.orc_pool_gradients_pull(n_so, hh, gg, _c(keys, np.uint64), _c(amps, np.float64), len(keys), sub, len(sub), out)
+    return out

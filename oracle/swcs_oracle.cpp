@@ -513,4 +513,60 @@ void orc_energy_grad(int n_so, int n_e, const double* h, const double* g, const 
   }
 }
 
+// sigma_E = sum_{D in S} <E|H|D> c_D at arbitrary determinants E, each
+// computed on its own from E's connections (pull form): E itself and every
+// single and double excitation of E that is in the state.
+void orc_sigma_at(int n_so, const double* h, const double* g, const uint64_t* keys, const double* amps, int64_t n,
+                  const uint64_t* at, int64_t n_at, double* out) {
+  Ham H{n_so, h, g};
+  std::unordered_map<det_t, double> s;
+  s.reserve(2 * n);
+  for (int64_t i = 0; i < n; ++i) s[keys[i]] += amps[i];
+  for (int64_t t = 0; t < n_at; ++t) {
+    const det_t e = at[t];
+    double acc = 0.0;
+    auto it = s.find(e);
+    if (it != s.end()) acc += sc_diag(H, e) * it->second;
+    // <E|H|D> for D = excitation of E equals <D|H|E> (real symmetric H)
+    for_each_connection(H, e, [&](det_t d, double v) {
+      auto jt = s.find(d);
+      if (jt != s.end()) acc += v * jt->second;
+    });
+    out[t] = acc;
+  }
+}
+
+// Pool gradient of the listed operators with sigma pulled at each needed E:
+// g_k = 2/<psi|psi> sum_D c_D (s sigma(tau_k D) - s' sigma(tau_k^dag D)).
+void orc_pool_gradients_pull(int n_so, const double* h, const double* g, const uint64_t* keys, const double* amps,
+                             int64_t n, const int64_t* subset, int64_t n_subset, double* g_out) {
+  Ham H{n_so, h, g};
+  std::unordered_map<det_t, double> s;
+  s.reserve(2 * n);
+  double n2 = 0.0;
+  for (int64_t i = 0; i < n; ++i) { s[keys[i]] += amps[i]; n2 += amps[i] * amps[i]; }
+  std::vector<Op> pool = gsd_pool(n_so);
+  auto sigma = [&](det_t e) {
+    double acc = 0.0;
+    auto it = s.find(e);
+    if (it != s.end()) acc += sc_diag(H, e) * it->second;
+    for_each_connection(H, e, [&](det_t d, double v) {
+      auto jt = s.find(d);
+      if (jt != s.end()) acc += v * jt->second;
+    });
+    return acc;
+  };
+  for (int64_t t = 0; t < n_subset; ++t) {
+    const Op& o = pool[subset[t]];
+    double acc = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      Term up = apply_tau(o, keys[i]);
+      if (!up.zero) acc += amps[i] * (up.sign * sigma(up.det));
+      Term dn = apply_tau_dag(o, keys[i]);
+      if (!dn.zero) acc -= amps[i] * (dn.sign * sigma(dn.det));
+    }
+    g_out[t] = 2.0 * acc / n2;
+  }
+}
+
 }  // extern "C"

@@ -981,6 +981,34 @@ int swcs_sweep_energy(swcs_ctx* c, double* e_out, double* n2_out) {
   return SWCS_OK;
 }
 
+int swcs_get_sigma(swcs_ctx* c, uint64_t* keys, double* sigma, int64_t cap, int64_t* n_out) {
+  int r = need_state(c);
+  if (r) return r;
+  const int64_t n = host_state_size(c);
+  if (n < 0) return fail(c, SWCS_ERR_CUDA, "cannot read state size");
+  if (n_out) *n_out = n;
+  if (cap < n) return SWCS_OK;
+  if ((r = ensure(c, c->sigma, (size_t)std::max<int64_t>(n, 1) * 8))) return r;
+  Ctrl* k = ctrl(c);
+  CK(cudaMemsetAsync(k->acc, 0, 16, c->st));
+  CK(launch_k(c, kKEnergy, [&] {
+    return launch_energy_sigma(ham_dev(c), state_dev(c), k->acc, (double*)c->sigma.p, c->nsm * sigma_blocks_per_sm(), c->st);
+  }));
+  std::vector<uint64_t> kk(n);
+  std::vector<double> ss(n);
+  CK(cudaMemcpyAsync(kk.data(), c->keys_a.p, 8 * n, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(ss.data(), c->sigma.p, 8 * n, cudaMemcpyDeviceToHost, c->st));
+  if ((r = check_device(c, "swcs_get_sigma"))) return r;
+  std::vector<int64_t> ord(n);
+  for (int64_t i = 0; i < n; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return kk[x] < kk[y]; });
+  for (int64_t i = 0; i < n; ++i) {
+    keys[i] = kk[ord[i]];
+    sigma[i] = ss[ord[i]];
+  }
+  return SWCS_OK;
+}
+
 int swcs_pool_features_dev(swcs_ctx* c, uint16_t* d_x) {
   int r = need_state(c);
   if (r) return r;

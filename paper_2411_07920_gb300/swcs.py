@@ -81,6 +81,7 @@ _SIGS = {
     "swcs_mlp_sync": ([_vp], _i),
     "swcs_log_abs_dev": ([_vp, _i64, _vp, _vp], _i),
     "swcs_pool_features_dev": ([_vp, _vp], _i),
+    "swcs_get_sigma": ([_vp, _vp, _vp, _i64, _p64], _i),
     "swcs_pool_screen_dev": ([_vp, _vp, ctypes.c_double, _vp, _p64], _i),
 }
 
@@ -376,6 +377,14 @@ class Context:
         m = ctypes.c_int64()
         self._ck(lib.swcs_get_state(self._h, _ptr(k), _ptr(a), n, ctypes.byref(m)))
         return k[:m.value], a[:m.value]
+
+    def get_sigma(self):
+        n = self.state_size()
+        k = np.zeros(max(n, 1), np.uint64)
+        sg = np.zeros(max(n, 1), np.float64)
+        m = ctypes.c_int64()
+        self._ck(lib.swcs_get_sigma(self._h, _ptr(k), _ptr(sg), n, ctypes.byref(m)))
+        return k[:m.value], sg[:m.value]
 
     def set_state(self, keys, amps):
         keys = _c(keys, np.uint64)

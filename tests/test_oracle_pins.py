@@ -307,3 +307,26 @@ def test_adjoint_truncated_matches_finite_differences(n_keep):
         assert abs(fd - d[g]) < 1e-7
         checked += 1
     assert checked >= len(w.ops) // 2
+
+
+def test_pull_routes_match_push_routes():
+    """sigma pulled at single determinants and the pull-form pool gradient
+    against the push-form sigma (internal energy route) and pool gradient."""
+    w = I.small_case(12, 4, 20, 81, n_keep=60)
+    k, a = O.apply_ansatz(w.n_so, w.n_e, w.ops, w.theta, 60)
+    sig = O.sigma_internal(w.n_so, w.h, w.g, k, a)
+    assert np.abs(O.sigma_at(w.n_so, w.h, w.g, k, a, k) - sig).max() < 1e-13
+    g = O.pool_gradients(w.n_so, w.h, w.g, k, a)
+    sub = np.arange(0, len(g), 7, dtype=np.int64)
+    gp = O.pool_gradients_pull(w.n_so, w.h, w.g, k, a, sub)
+    assert np.abs(gp - g[sub]).max() < 1e-13
+    # sigma outside the state equals the dense H psi there
+    basis = J.sector(w.n_so, w.n_e)
+    H = J.hamiltonian_sector(w.n_so, w.h, w.g, basis)
+    psi = np.zeros(len(basis))
+    idx = {int(b): i for i, b in enumerate(basis)}
+    for kk, aa in zip(k, a):
+        psi[idx[int(kk)]] = aa
+    hp = H @ psi
+    pick = basis[::5].astype(np.uint64)
+    assert np.abs(O.sigma_at(w.n_so, w.h, w.g, k, a, pick) - hp[::5]).max() < 1e-12
