@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--cluster", type=int, default=2, help="CTAs per alpha-string row cluster")
     p.add_argument("--rows-l2", type=int, default=0, help="1: cap concurrent rows to about half of L2")
     p.add_argument("--threads", type=int, default=512, help="threads per CTA of the row sweep")
+    p.add_argument("--row-clusters", type=int, default=0, help="clusters of the row sweep (0: as many as fit)")
+    p.add_argument("--row-occupancy", type=int, default=3, help="resident 512-thread row-sweep CTAs per SM (2 or 3)")
     p.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched leg")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     p.add_argument("--no-screen", action="store_true", help="skip the learned-screening leg")
@@ -184,6 +186,8 @@ def run_swcs(args):
     ctx.set_option("cluster", args.cluster)
     ctx.set_option("rows_l2", args.rows_l2)
     ctx.set_option("threads", args.threads)
+    ctx.set_option("row_clusters", args.row_clusters)
+    ctx.set_option("row_occupancy", args.row_occupancy)
     pool = ctx.pool_size()
     dev = torch.device("cuda", local)
     d_ops = torch.from_numpy(w.ops.reshape(-1).copy()).to(dev)

@@ -147,6 +147,8 @@ int swcs_stats(swcs_ctx* ctx, int64_t* h_out8);
  *              beta-string space exceeds 2^22 or clusters cannot launch)
  *   "cluster"  CTAs per alpha-string row in the row sweep, 1..16 (default 2)
  *   "threads"  threads per CTA of the row sweep: 128, 256 or 512 (default 512)
+ *   "row_occupancy" resident 512-thread CTAs per SM the row sweep is compiled
+ *              for: 3 (default, register-capped) or 2
  *   "gate_blocks"   CTAs of the persistent gate kernel (0, default: whole device)
  *   "row_clusters"  clusters of the row sweep (0, default: as many as fit)
  *   "rows_l2"  1: cap the row sweep's concurrent rows to about half of L2;

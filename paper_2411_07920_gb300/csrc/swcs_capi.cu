@@ -55,13 +55,14 @@ struct swcs_ctx {
   DevBuf gdev, subset_dev, gsub;
 
   // row sweep: alpha strings of the sector, beta-rank tables, grouped state, rows
-  DevBuf alpha_list, rank_tab, atab, gid_of, gcount, goff, gfill, gkey, gamp, grank, rows;
+  DevBuf alpha_list, rank_tab, atab, gid_of, gcount, goff, gfill, gkey, gamp, grank, rows, rbeta, gab, kab;
   int NA = 0;
   int64_t NB = 0;
   int opt_sweep = 0;    // 0 auto, 1 hashed external table, 2 alpha-string rows
   int opt_cluster = 2;  // CTAs per row cluster
   int opt_rows_l2 = 0;  // cap concurrent rows to about half of L2
   int opt_threads = 512;  // threads per CTA of the row sweep
+  int opt_row_occ = 3;    // resident 512-thread CTAs per SM asked of the compiler (2 or 3)
   int opt_gate_blocks = 0;   // CTAs of the gate kernel (0: whole device)
   int opt_row_clusters = 0;  // clusters of the row sweep (0: as many as fit)
 
@@ -457,7 +458,7 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
   if (smem > 96 * 1024) return 1;
   int ncl = 0;
   const int nthr = c->opt_threads;
-  if (row_sweep_max_clusters(nthr, gsz, smem, &ncl) != cudaSuccess || ncl <= 0) {
+  if (row_sweep_max_clusters(nthr, c->opt_row_occ, gsz, smem, &ncl) != cudaSuccess || ncl <= 0) {
     cudaGetLastError();
     return 1;
   }
@@ -474,7 +475,8 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
       (r = ensure(c, c->gcount, nd * 8 + 8)) || (r = ensure(c, c->goff, nd * 8 + 16)) ||
       (r = ensure(c, c->gfill, nd * 8 + 8)) || (r = ensure(c, c->gkey, nd * 8 + 8)) ||
       (r = ensure(c, c->gamp, nd * 8 + 8)) || (r = ensure(c, c->grank, nd * 4 + 4)) ||
-      (r = ensure(c, c->rows, (size_t)ncl * c->NB * 8)))
+      (r = ensure(c, c->rows, (size_t)ncl * c->NB * 8)) ||
+      (r = ensure(c, c->rbeta, (size_t)std::max<int64_t>(nd, 1) * ks * nvs * 4)))
     return r;
   if (!enqueue) return SWCS_OK;
   CK(cudaMemsetAsync(c->atab.p, 0xff, acap * sizeof(IdxSlot), c->st));
@@ -503,6 +505,9 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
   ga.acc = k->acc;
   CK(launch_k(c, kKGroup, [&] { return launch_group_state(ga, c->st); }));
   c->launches += 4;  // five grouping kernels in one call
+  CK(launch_k(c, kKGroup, [&] {
+    return launch_rbeta(ga.gkey, ga.n, ga.rank_tab, ks, nvs, m, (uint32_t*)c->rbeta.p, c->st);
+  }));
   RowArgs ra;
   ra.H = ham_dev(c);
   ra.gkey = ga.gkey;
@@ -523,7 +528,10 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
   ra.max_ent_d = max_d;
   ra.touched_words = twords;
   ra.sel_bits = sel;
-  CK(launch_k(c, kKRow, [&] { return launch_row_sweep(ra, nthr, gsz, ncl, smem, c->st); }));
+  ra.rbeta = (const uint32_t*)c->rbeta.p;
+  ra.gab = (const double*)c->gab.p;
+  ra.kab = (const int*)c->kab.p;
+  CK(launch_k(c, kKRow, [&] { return launch_row_sweep(ra, nthr, c->opt_row_occ, gsz, ncl, smem, c->st); }));
   c->stats[2] = 0;
   c->stats[3] = ncl;
   c->stats[4] = (int64_t)ncl * c->NB;
@@ -662,6 +670,7 @@ int swcs_destroy(swcs_ctx* c) {
                     &c->keys_b, &c->amps_b, &c->tab0, &c->tab1, &c->ctrl, &c->ops_dev, &c->cs_dev,
                     &c->gdev, &c->subset_dev, &c->gsub, &c->ext, &c->alpha_list, &c->rank_tab, &c->atab,
                     &c->gid_of, &c->gcount, &c->goff, &c->gfill, &c->gkey, &c->gamp, &c->grank, &c->rows,
+                    &c->rbeta, &c->gab, &c->kab,
                     &c->ck_keys, &c->ck_amps, &c->ck_n, &c->sn_keys, &c->sn_amps, &c->sn_n, &c->sigma, &c->nu0,
                     &c->nu1, &c->atab0, &c->atab1, &c->dth, &c->pool_dev, &c->selbits, &c->feat,
                     &c->ypred, &c->topk_hist, &c->topk_ctl, &c->occ};
@@ -733,6 +742,50 @@ int swcs_load_hamiltonian(swcs_ctx* c, const double* h_h, const double* h_g, int
           T[((size_t)ch * (ks + 1) + j) * 256 + byte] = ok ? (uint32_t)r : 0u;
         }
     if ((r = ensure(c, c->alpha_list, al.size() * 4 + 4)) || (r = ensure(c, c->rank_tab, T.size() * 4))) return r;
+    // alpha-beta double tables by spatial indices: the phase of the double on
+    // any D is (beta single on D) ^ (alpha single on D) ^ e(a,b,i,j), and e
+    // depends on the indices only, so it is read off a minimal determinant
+    if (m <= 32) {
+      const size_t m4 = (size_t)m * m * m * m;
+      std::vector<double> gab(m4, 0.0);
+      std::vector<int> kab(m4, -1);
+      auto par_below = [](uint64_t d, int p) { return __builtin_popcountll(d & ((1ull << p) - 1ull)) & 1; };
+      auto sphase = [&](uint64_t d, int a0, int c1) { return par_below(d, a0) ^ par_below(d & ~(1ull << a0), c1); };
+      auto dphase = [&](uint64_t d, int p, int q, int rr, int ss) {
+        int par = par_below(d, p);
+        uint64_t x = d & ~(1ull << p);
+        par ^= par_below(x, q);
+        x &= ~(1ull << q);
+        par ^= par_below(x, ss);
+        x |= (1ull << ss);
+        par ^= par_below(x, rr);
+        return par;
+      };
+      const size_t n1 = (size_t)n;
+      for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) {
+          if (a == b) continue;
+          for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) {
+              if (i == j) continue;
+              const int A2 = 2 * a, B2 = 2 * b, I1 = 2 * i + 1, J1 = 2 * j + 1;
+              const int p = std::min(A2, I1), q = std::max(A2, I1), rr = std::min(B2, J1), ss = std::max(B2, J1);
+              const uint64_t d0 = (1ull << A2) | (1ull << I1);
+              const int e = dphase(d0, p, q, rr, ss) ^ sphase(d0, I1, J1) ^ sphase(d0, A2, B2);
+              const double v = h_g[((rr * n1 + ss) * n1 + p) * n1 + q];  // <rs||pq>
+              const size_t ti = (((size_t)a * m + b) * m + i) * m + j;
+              gab[ti] = e ? -v : v;
+              const int pa = pair_index(p, q, n), pb = pair_index(rr, ss, n);
+              const bool down = pa > pb;
+              const int k = down ? opd[(size_t)pb * c->npairs + pa] : opd[(size_t)pa * c->npairs + pb];
+              kab[ti] = k | (int)((unsigned)(e ^ (int)down) << 31);
+            }
+        }
+      if ((r = ensure(c, c->gab, m4 * 8)) || (r = ensure(c, c->kab, m4 * 4))) return r;
+      CK(cudaMemcpyAsync(c->gab.p, gab.data(), m4 * 8, cudaMemcpyHostToDevice, c->st));
+      CK(cudaMemcpyAsync(c->kab.p, kab.data(), m4 * 4, cudaMemcpyHostToDevice, c->st));
+      CK(cudaStreamSynchronize(c->st));
+    }
     if (!al.empty()) CK(cudaMemcpyAsync(c->alpha_list.p, al.data(), al.size() * 4, cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(c->rank_tab.p, T.data(), T.size() * 4, cudaMemcpyHostToDevice, c->st));
   }
@@ -1055,6 +1108,9 @@ int swcs_set_option(swcs_ctx* c, const char* name, int64_t value) {
   } else if (k == "row_clusters") {
     if (value < 0) return fail(c, SWCS_ERR_INVALID_ARG, "row_clusters must be >= 0");
     c->opt_row_clusters = (int)value;
+  } else if (k == "row_occupancy") {
+    if (value != 2 && value != 3) return fail(c, SWCS_ERR_INVALID_ARG, "row_occupancy must be 2 or 3");
+    c->opt_row_occ = (int)value;
   } else if (k == "threads") {
     if (value != 128 && value != 256 && value != 512) return fail(c, SWCS_ERR_INVALID_ARG, "threads must be 128, 256 or 512");
     c->opt_threads = (int)value;

@@ -121,6 +121,14 @@ struct RowArgs {
   int max_ent_s, max_ent_d;
   int touched_words;  // words of the per-CTA touched-entry bitmap (0: clear whole rows)
   const uint32_t* sel_bits;  // pool operators to evaluate (nullptr: all)
+  // beta single excitations of each grouped determinant, t = occ_slot*nv + vir_slot:
+  // rank of the new beta string | (phase bit << 31)
+  const uint32_t* rbeta;
+  // alpha-beta doubles by spatial indices (a -> b alpha, i -> j beta), [m^4]:
+  // integral with the index-only part of the phase folded in, and the pool
+  // index | (direction and index-only phase bit << 31)
+  const double* gab;
+  const int* kab;
 };
 
 struct GroupArgs {
@@ -143,9 +151,12 @@ struct GroupArgs {
 };
 
 size_t row_sweep_smem(int max_ent_s, int max_ent_d, int t_same, int touched_words);
-cudaError_t row_sweep_max_clusters(int threads, int gsz, size_t smem, int* n_clusters);
-cudaError_t launch_row_sweep(const RowArgs& a, int threads, int gsz, int n_clusters, size_t smem, cudaStream_t st);
+cudaError_t row_sweep_max_clusters(int threads, int occ, int gsz, size_t smem, int* n_clusters);
+cudaError_t launch_row_sweep(const RowArgs& a, int threads, int occ, int gsz, int n_clusters, size_t smem,
+                             cudaStream_t st);
 cudaError_t launch_group_state(const GroupArgs& g, cudaStream_t st);
+cudaError_t launch_rbeta(const uint64_t* gkey, const long long* n, const uint32_t* rank_tab, int ks, int nv, int m,
+                         uint32_t* rbeta, cudaStream_t st);
 
 // Adjoint (swcs_adjoint.cu).
 cudaError_t launch_build_index(const uint64_t* keys, const long long* n, IdxSlot* tab, uint64_t mask, cudaStream_t st);

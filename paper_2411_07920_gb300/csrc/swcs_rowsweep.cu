@@ -234,10 +234,20 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
     for (int t = max(1, ch * kSameChunk) + lane; t < t_end; t += 32) {
       const uint32_t code = dy.same_tab[t];
       const int o1 = code & 255, o2 = (code >> 8) & 255, v1 = (code >> 16) & 255, v2 = code >> 24;
-      if (o2 == 255) {
+      if (o2 == 255) {  // beta single: rank and phase precomputed for this determinant
         const int i = sh.bocc[warp][o1], jv = sh.bvir[warp][v1];
-        const uint32_t re = str_rank(A.rank_tab, ks, db ^ (1u << i) ^ (1u << jv));
-        row_pair<SCATTER>(A, row, touched, d, cd, re, 2 * i + 1, -1, 2 * jv + 1, -1, oa);
+        const uint32_t wb = __ldg(&A.rbeta[(size_t)di * (ks * nvs) + o1 * nvs + v1]);
+        const uint32_t re = wb & 0x7FFFFFFFu;
+        const int sb = (int)(wb >> 31);
+        const int p = 2 * i + 1, r = 2 * jv + 1;
+        if (SCATTER) {
+          atomicAdd(&row[re], apply_sign(fock_single(A, oa, p, r), sb) * cd);
+          mark(touched, re);
+        } else {
+          const int k = A.H.ops1[(p < r ? p : r) * A.H.n + (p < r ? r : p)];
+          if (!A.sel_bits || ((__ldg(&A.sel_bits[k >> 5]) >> (k & 31)) & 1u))
+            atomicAdd(&A.g[k], apply_sign(cd * row[re], sb ^ (int)(p > r)));
+        }
       } else {
         const int i1 = sh.bocc[warp][o1], i2 = sh.bocc[warp][o2];
         const int j1 = sh.bvir[warp][v1], j2 = sh.bvir[warp][v2];
@@ -259,11 +269,50 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
     const uint8_t* oa = sh.occ_all[warp];
     const int pa = en.o[0], pb = en.o[2];  // alpha spin-orbitals: removed, added
     if (lane == 0) row_pair<SCATTER>(A, row, touched, d, cd, A.grank[di], pa, -1, pb, -1, oa);
-    for (int t2 = lane; t2 < ks * nvs; t2 += 32) {
-      const int i = sh.bocc[warp][t2 / nvs], j = sh.bvir[warp][t2 % nvs];
-      const int bi = 2 * i + 1, bj = 2 * j + 1;
-      const uint32_t re = str_rank(A.rank_tab, ks, db ^ (1u << i) ^ (1u << j));
-      row_pair<SCATTER>(A, row, touched, d, cd, re, min(pa, bi), max(pa, bi), min(pb, bj), max(pb, bj), oa);
+    // alpha-beta doubles: phase = (beta single on D) ^ (alpha single on D) ^ (index-only bit in the tables)
+    const int sa = single_phase(d, pa, pb);
+    const size_t base = ((size_t)(pa >> 1) * m + (pb >> 1)) * (size_t)m * m;
+    const uint32_t* rb = A.rbeta + (size_t)di * (ks * nvs);
+    const int nsb = ks * nvs;
+    if (SCATTER) {
+      for (int t2 = lane; t2 < nsb; t2 += 32) {
+        const int i = sh.bocc[warp][t2 / nvs], j = sh.bvir[warp][t2 % nvs];
+        const uint32_t wb = __ldg(&rb[t2]);
+        const uint32_t re = wb & 0x7FFFFFFFu;
+        const int sb = (int)(wb >> 31) ^ sa;
+        atomicAdd(&row[re], apply_sign(__ldg(&A.gab[base + (size_t)i * m + j]), sb) * cd);
+        mark(touched, re);
+      }
+    } else {
+      // four targets per lane with their row reads issued together
+      for (int t0 = 0; t0 < nsb; t0 += 128) {
+        uint32_t re[4];
+        int kk[4], sb[4];
+        double sv[4];
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int t2 = t0 + u * 32 + lane;
+          ok[u] = t2 < nsb;
+          re[u] = 0;
+          kk[u] = 0;
+          sb[u] = 0;
+          if (ok[u]) {
+            const int i = sh.bocc[warp][t2 / nvs], j = sh.bvir[warp][t2 % nvs];
+            const uint32_t wb = __ldg(&rb[t2]);
+            re[u] = wb & 0x7FFFFFFFu;
+            sb[u] = (int)(wb >> 31) ^ sa;
+            kk[u] = __ldg(&A.kab[base + (size_t)i * m + j]);
+            const int k = kk[u] & 0x7FFFFFFF;
+            if (A.sel_bits && !((__ldg(&A.sel_bits[k >> 5]) >> (k & 31)) & 1u)) ok[u] = false;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sv[u] = ok[u] ? row[re[u]] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (ok[u]) atomicAdd(&A.g[kk[u] & 0x7FFFFFFF], apply_sign(cd * sv[u], sb[u] ^ (int)((unsigned)kk[u] >> 31)));
+      }
     }
     __syncwarp();
   }
@@ -284,8 +333,8 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
   }
 }
 
-template <int kRowThreads>
-__global__ void __launch_bounds__(kRowThreads)
+template <int kRowThreads, int kMinBlocks>
+__global__ void __launch_bounds__(kRowThreads, kMinBlocks)
 row_sweep_kernel(RowArgs A) {
   constexpr int kRowWarps = kRowThreads / 32;
   extern __shared__ __align__(16) unsigned char dyn[];
@@ -505,14 +554,47 @@ __global__ void group_scatter_kernel(const uint64_t* keys, const double* amps, c
   }
 }
 
+// Beta single excitations of every grouped determinant: rank of the new beta
+// string and the phase bit of a+_{2j+1} a_{2i+1} on D, t = occ_slot*nv + vir_slot.
+__global__ void rbeta_kernel(const uint64_t* gkey, const long long* n_ptr, const uint32_t* rank_tab, int ks, int nv,
+                             int m, uint32_t* rbeta) {
+  const long long n = *n_ptr;
+  const int lane = threadIdx.x & 31;
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long di = w0; di < n; di += nw) {
+    const uint64_t d = gkey[di];
+    const uint32_t db = even_bits(d >> 1);
+    // slot -> orbital via the o-th set / unset bit of the beta string
+    for (int t = lane; t < ks * nv; t += 32) {
+      const int o = t / nv, v = t - o * nv;
+      uint32_t x = db;
+      for (int c = 0; c < o; ++c) x &= x - 1;
+      const int i = __ffs(x) - 1;
+      uint32_t y = ~db & ((m >= 32) ? 0xFFFFFFFFu : ((1u << m) - 1u));
+      for (int c = 0; c < v; ++c) y &= y - 1;
+      const int j = __ffs(y) - 1;
+      const uint32_t re = str_rank(rank_tab, ks, db ^ (1u << i) ^ (1u << j));
+      const int sb = single_phase(d, 2 * i + 1, 2 * j + 1);
+      rbeta[(size_t)di * (ks * nv) + t] = re | ((uint32_t)sb << 31);
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_rbeta(const uint64_t* gkey, const long long* n, const uint32_t* rank_tab, int ks, int nv, int m,
+                         uint32_t* rbeta, cudaStream_t st) {
+  rbeta_kernel<<<1216, 256, 0, st>>>(gkey, n, rank_tab, ks, nv, m, rbeta);
+  return cudaGetLastError();
+}
 
 size_t row_sweep_smem(int max_ent_s, int max_ent_d, int t_same, int touched_words) {
   return sizeof(RowEnt) * (size_t)(max_ent_s + max_ent_d) + 4 * (size_t)t_same + 4 * (size_t)touched_words;
 }
 
 namespace {
-template <int NT>
+template <int NT, int MB>
 cudaError_t max_clusters_t(int gsz, size_t smem, int* n_clusters) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(gsz * 64);
@@ -525,16 +607,16 @@ cudaError_t max_clusters_t(int gsz, size_t smem, int* n_clusters) {
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaFuncSetAttribute(row_sweep_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(row_sweep_kernel<NT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (gsz > 8) {
-    e = cudaFuncSetAttribute(row_sweep_kernel<NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(row_sweep_kernel<NT, MB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
-  return cudaOccupancyMaxActiveClusters(n_clusters, row_sweep_kernel<NT>, &cfg);
+  return cudaOccupancyMaxActiveClusters(n_clusters, row_sweep_kernel<NT, MB>, &cfg);
 }
 
-template <int NT>
+template <int NT, int MB>
 cudaError_t launch_t(const RowArgs& a, int gsz, int n_clusters, size_t smem, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(gsz * n_clusters);
@@ -548,21 +630,26 @@ cudaError_t launch_t(const RowArgs& a, int gsz, int n_clusters, size_t smem, cud
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, row_sweep_kernel<NT>, a);
+  return cudaLaunchKernelEx(&cfg, row_sweep_kernel<NT, MB>, a);
 }
 }  // namespace
 
-cudaError_t row_sweep_max_clusters(int threads, int gsz, size_t smem, int* n_clusters) {
-  if (threads == 128) return max_clusters_t<128>(gsz, smem, n_clusters);
-  if (threads == 256) return max_clusters_t<256>(gsz, smem, n_clusters);
-  if (threads == 512) return max_clusters_t<512>(gsz, smem, n_clusters);
+// threads: 128, 256 or 512 per CTA; resident 512-thread CTAs per SM requested
+// from the compiler: 2 (no register cap) or 3 (40 registers)
+cudaError_t row_sweep_max_clusters(int threads, int occ, int gsz, size_t smem, int* n_clusters) {
+  if (threads == 128) return max_clusters_t<128, 1>(gsz, smem, n_clusters);
+  if (threads == 256) return max_clusters_t<256, 1>(gsz, smem, n_clusters);
+  if (threads == 512) return occ >= 3 ? max_clusters_t<512, 3>(gsz, smem, n_clusters)
+                                      : max_clusters_t<512, 1>(gsz, smem, n_clusters);
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_row_sweep(const RowArgs& a, int threads, int gsz, int n_clusters, size_t smem, cudaStream_t st) {
-  if (threads == 128) return launch_t<128>(a, gsz, n_clusters, smem, st);
-  if (threads == 256) return launch_t<256>(a, gsz, n_clusters, smem, st);
-  if (threads == 512) return launch_t<512>(a, gsz, n_clusters, smem, st);
+cudaError_t launch_row_sweep(const RowArgs& a, int threads, int occ, int gsz, int n_clusters, size_t smem,
+                             cudaStream_t st) {
+  if (threads == 128) return launch_t<128, 1>(a, gsz, n_clusters, smem, st);
+  if (threads == 256) return launch_t<256, 1>(a, gsz, n_clusters, smem, st);
+  if (threads == 512) return occ >= 3 ? launch_t<512, 3>(a, gsz, n_clusters, smem, st)
+                                      : launch_t<512, 1>(a, gsz, n_clusters, smem, st);
   return cudaErrorInvalidValue;
 }
 

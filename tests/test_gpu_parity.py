@@ -93,17 +93,18 @@ def test_energy_and_pool_gradient_truncated(S, n_so, n_e, n_ops, seed, n_keep):
     assert np.abs(gs[sub] - go[sub]).max() < TOL
 
 
-@pytest.mark.parametrize("sweep,cluster,threads", [(1, 4, 512), (2, 1, 128), (2, 2, 256), (2, 4, 512), (2, 8, 512),
-                                                   (2, 1, 512)])
+@pytest.mark.parametrize("sweep,cluster,threads,occ", [(1, 4, 512, 3), (2, 1, 128, 3), (2, 2, 256, 3), (2, 4, 512, 3),
+                                                       (2, 8, 512, 2), (2, 1, 512, 2), (2, 2, 512, 3)])
 @pytest.mark.parametrize("n_so,n_e,n_ops,seed,n_keep", [(16, 6, 40, 102, 150), (24, 8, 40, 107, 400),
                                                         (28, 8, 60, 104, 3000), (12, 4, 10, 1, 0)])
-def test_sweep_paths_match_oracle(S, sweep, cluster, threads, n_so, n_e, n_ops, seed, n_keep):
+def test_sweep_paths_match_oracle(S, sweep, cluster, threads, occ, n_so, n_e, n_ops, seed, n_keep):
     """Hashed external-sigma sweep and alpha-string row sweep, several launch shapes."""
     w = I.small_case(n_so, n_e, n_ops, seed, n_keep=n_keep)
     c = ctx_for(S, w)
     c.set_option("sweep", sweep)
     c.set_option("cluster", cluster)
     c.set_option("threads", threads)
+    c.set_option("row_occupancy", occ)
     c.apply_ansatz(w.ops, w.theta, n_keep)
     ko, ao = O.apply_ansatz(w.n_so, w.n_e, w.ops, w.theta, n_keep)
     g = c.pool_gradients()
