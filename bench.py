@@ -279,7 +279,7 @@ def run_swcs(args):
         bytes_per_launch = 16.0 * pairs
     achieved = bytes_per_launch / (dom_ms / dom_n / 1e3) / 1e9
     roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": achieved / hbm_peak, "traffic": None,
+            "frac": achieved / hbm_peak, "traffic": measured_traffic(dom),
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     gate_ms = prof.get("ansatz", (0.0, 0))[0]
     gate_dets_per_s = stats["gate_dets"] / (gate_ms / 1e3) if gate_ms > 0 else None
@@ -358,6 +358,24 @@ def run_swcs(args):
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch of the dominant kernel from its committed ncu summary,
+    only while the kernel's source is the one that was captured (else None)."""
+    import hashlib
+    files = {"row_sweep": ("profiles/row_sweep_so52_e12_N1e6.md", "paper_2411_07920_gb300/csrc/swcs_rowsweep.cu")}
+    if kernel not in files:
+        return None
+    summary, src = (os.path.join(ROOT, f) for f in files[kernel])
+    try:
+        text = open(summary).read()
+        want = text.split("source_sha256:")[1].split()[0]
+        traffic = int(text.split("traffic_bytes_per_launch:")[1].split()[0])
+        have = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except (OSError, IndexError, ValueError):
+        return None
+    return traffic if have == want else None
 
 
 def run_screen_leg(swcs, ctx, w, args, torch, frac=0.05):
