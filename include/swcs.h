@@ -147,6 +147,9 @@ int swcs_stats(swcs_ctx* ctx, int64_t* h_out8);
  *              beta-string space exceeds 2^22 or clusters cannot launch)
  *   "cluster"  CTAs per alpha-string row in the row sweep, 1..16 (default 2)
  *   "threads"  threads per CTA of the row sweep: 128, 256 or 512 (default 512)
+ *   "energy"   energy and sigma_D: 0 automatic (alpha-string rows when the
+ *              sector allows, default), 1 probe kernel (connections of each D
+ *              looked up in the state's index), 2 rows
  *   "row_occupancy" resident 512-thread CTAs per SM the row sweep is compiled
  *              for: 3 (default, register-capped) or 2
  *   "gate_blocks"   CTAs of the persistent gate kernel (0, default: whole device)

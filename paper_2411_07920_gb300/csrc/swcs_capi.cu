@@ -55,7 +55,7 @@ struct swcs_ctx {
   DevBuf gdev, subset_dev, gsub;
 
   // row sweep: alpha strings of the sector, beta-rank tables, grouped state, rows
-  DevBuf alpha_list, rank_tab, atab, gid_of, gcount, goff, gfill, gkey, gamp, grank, rows, rbeta, gab, kab;
+  DevBuf alpha_list, rank_tab, atab, gid_of, gcount, goff, gfill, gkey, gamp, grank, rows, rbeta, gab, kab, gorig;
   int NA = 0;
   int64_t NB = 0;
   int opt_sweep = 0;    // 0 auto, 1 hashed external table, 2 alpha-string rows
@@ -63,6 +63,7 @@ struct swcs_ctx {
   int opt_rows_l2 = 0;  // cap concurrent rows to about half of L2
   int opt_threads = 512;  // threads per CTA of the row sweep
   int opt_row_occ = 3;    // resident 512-thread CTAs per SM asked of the compiler (2 or 3)
+  int opt_energy = 0;     // energy: 0 automatic, 1 probe kernel, 2 alpha-string rows
   int opt_gate_blocks = 0;   // CTAs of the gate kernel (0: whole device)
   int opt_row_clusters = 0;  // clusters of the row sweep (0: as many as fit)
 
@@ -438,7 +439,8 @@ __global__ void sincos_kernel(const double* th, double* cs, int n) {
 // Alpha-string row sweep; returns 1 when not applicable (caller falls back).
 // nd_bound >= 0: size buffers for that many determinants instead of reading
 // the state size (no host synchronisation); enqueue = false: only size.
-int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = true, const uint32_t* sel = nullptr) {
+int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = true, const uint32_t* sel = nullptr,
+               bool energy_only = false, double* sig_out = nullptr) {
   const int m = c->n / 2;
   if (m > 32 || c->NB <= 0 || c->NB > (1 << 22)) return 1;
   const int64_t nd = nd_bound >= 0 ? nd_bound : host_state_size(c);
@@ -476,7 +478,8 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
       (r = ensure(c, c->gfill, nd * 8 + 8)) || (r = ensure(c, c->gkey, nd * 8 + 8)) ||
       (r = ensure(c, c->gamp, nd * 8 + 8)) || (r = ensure(c, c->grank, nd * 4 + 4)) ||
       (r = ensure(c, c->rows, (size_t)ncl * c->NB * 8)) ||
-      (r = ensure(c, c->rbeta, (size_t)std::max<int64_t>(nd, 1) * ks * nvs * 4)))
+      (r = ensure(c, c->rbeta, (size_t)std::max<int64_t>(nd, 1) * ks * nvs * 4)) ||
+      (r = ensure(c, c->gorig, (size_t)std::max<int64_t>(nd, 1) * 4)))
     return r;
   if (!enqueue) return SWCS_OK;
   CK(cudaMemsetAsync(c->atab.p, 0xff, acap * sizeof(IdxSlot), c->st));
@@ -484,7 +487,7 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
   CK(cudaMemsetAsync(c->gfill.p, 0, nd * 8 + 8, c->st));
   CK(cudaMemsetAsync(&k->n_distinct, 0, 8, c->st));
   CK(cudaMemsetAsync(k->acc, 0, 16, c->st));
-  CK(cudaMemsetAsync(d_g, 0, sizeof(double) * c->pool_size, c->st));
+  if (!energy_only) CK(cudaMemsetAsync(d_g, 0, sizeof(double) * c->pool_size, c->st));
   CK(cudaMemsetAsync(c->rows.p, 0, (size_t)ncl * c->NB * 8, c->st));
   GroupArgs ga;
   ga.keys = (const uint64_t*)c->keys_a.p;
@@ -500,6 +503,7 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
   ga.gkey = (uint64_t*)c->gkey.p;
   ga.gamp = (double*)c->gamp.p;
   ga.grank = (uint32_t*)c->grank.p;
+  ga.gorig = (uint32_t*)c->gorig.p;
   ga.rank_tab = (const uint32_t*)c->rank_tab.p;
   ga.ks = ks;
   ga.acc = k->acc;
@@ -531,13 +535,23 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
   ra.rbeta = (const uint32_t*)c->rbeta.p;
   ra.gab = (const double*)c->gab.p;
   ra.kab = (const int*)c->kab.p;
+  ra.energy_only = energy_only ? 1 : 0;
+  ra.sig_out = sig_out;
+  ra.gorig = (const uint32_t*)c->gorig.p;
   CK(launch_k(c, kKRow, [&] { return launch_row_sweep(ra, nthr, c->opt_row_occ, gsz, ncl, smem, c->st); }));
   c->stats[2] = 0;
   c->stats[3] = ncl;
   c->stats[4] = (int64_t)ncl * c->NB;
-  CK(launch_k(c, kKOther, [&] { return launch_scale_gradient(d_g, c->pool_size, k->acc, c->st); }));
+  if (!energy_only) CK(launch_k(c, kKOther, [&] { return launch_scale_gradient(d_g, c->pool_size, k->acc, c->st); }));
   CK(launch_k(c, kKOther, [&] { return launch_finalize_energy(k->acc, k->eout, c->st); }));
   return SWCS_OK;
+}
+
+// Energy (and optionally sigma_D in state order) through the row machinery;
+// 1 when not applicable.
+int energy_rows(swcs_ctx* c, double* sig_out) {
+  if (c->opt_energy == 1) return 1;
+  return sweep_rows(c, nullptr, -1, true, nullptr, true, sig_out);
 }
 
 int sweep(swcs_ctx* c, double* d_g, const uint32_t* sel = nullptr) {
@@ -670,7 +684,7 @@ int swcs_destroy(swcs_ctx* c) {
                     &c->keys_b, &c->amps_b, &c->tab0, &c->tab1, &c->ctrl, &c->ops_dev, &c->cs_dev,
                     &c->gdev, &c->subset_dev, &c->gsub, &c->ext, &c->alpha_list, &c->rank_tab, &c->atab,
                     &c->gid_of, &c->gcount, &c->goff, &c->gfill, &c->gkey, &c->gamp, &c->grank, &c->rows,
-                    &c->rbeta, &c->gab, &c->kab,
+                    &c->rbeta, &c->gab, &c->kab, &c->gorig,
                     &c->ck_keys, &c->ck_amps, &c->ck_n, &c->sn_keys, &c->sn_amps, &c->sn_n, &c->sigma, &c->nu0,
                     &c->nu1, &c->atab0, &c->atab1, &c->dth, &c->pool_dev, &c->selbits, &c->feat,
                     &c->ypred, &c->topk_hist, &c->topk_ctl, &c->occ};
@@ -880,6 +894,11 @@ int swcs_energy_dev(swcs_ctx* c, double* d_out) {
   int r = need_state(c);
   if (r) return r;
   Ctrl* k = ctrl(c);
+  if ((r = energy_rows(c, nullptr)) != 1) {
+    if (r) return r;
+    if (d_out) CK(cudaMemcpyAsync(d_out, k->eout, 16, cudaMemcpyDeviceToDevice, c->st));
+    return SWCS_OK;
+  }
   CK(cudaMemsetAsync(k->acc, 0, 16, c->st));
   CK(launch_k(c, kKEnergy, [&] { return launch_energy(ham_dev(c), state_dev(c), k->acc, c->nsm * sigma_blocks_per_sm(), c->st); }));
   CK(launch_k(c, kKOther, [&] { return launch_finalize_energy(k->acc, d_out ? d_out : k->eout, c->st); }));
@@ -1108,6 +1127,9 @@ int swcs_set_option(swcs_ctx* c, const char* name, int64_t value) {
   } else if (k == "row_clusters") {
     if (value < 0) return fail(c, SWCS_ERR_INVALID_ARG, "row_clusters must be >= 0");
     c->opt_row_clusters = (int)value;
+  } else if (k == "energy") {
+    if (value < 0 || value > 2) return fail(c, SWCS_ERR_INVALID_ARG, "energy must be 0, 1 or 2");
+    c->opt_energy = (int)value;
   } else if (k == "row_occupancy") {
     if (value != 2 && value != 3) return fail(c, SWCS_ERR_INVALID_ARG, "row_occupancy must be 2 or 3");
     c->opt_row_occ = (int)value;
@@ -1219,7 +1241,13 @@ int swcs_energy_grad(swcs_ctx* c, const uint8_t* h_ops, const double* h_theta, i
   // ---- energy, sigma and nu_M = P_M (H - E) psi_M on the final state
   CK(cudaMemsetAsync(k->acc, 0, 16, c->st));
   const int nblk = c->nsm * sigma_blocks_per_sm();
-  CK(launch_k(c, kKEnergy, [&] { return launch_energy_sigma(ham_dev(c), state_dev(c), k->acc, (double*)c->sigma.p, nblk, c->st); }));
+  c->have_state = true;
+  if ((r = energy_rows(c, (double*)c->sigma.p)) == 1) {
+    CK(cudaMemsetAsync(k->acc, 0, 16, c->st));
+    CK(launch_k(c, kKEnergy, [&] { return launch_energy_sigma(ham_dev(c), state_dev(c), k->acc, (double*)c->sigma.p, nblk, c->st); }));
+  } else if (r) {
+    return r;
+  }
   IdxSlot* atab[2] = {(IdxSlot*)c->atab0.p, (IdxSlot*)c->atab1.p};
   double* nu[2] = {(double*)c->nu0.p, (double*)c->nu1.p};
   CK(launch_k(c, kKOther, [&] { return launch_nu_init((const double*)c->amps_a.p, (const double*)c->sigma.p, &k->n_state, k->acc, nu[0], c->st); }));

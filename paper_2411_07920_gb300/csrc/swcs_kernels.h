@@ -129,6 +129,11 @@ struct RowArgs {
   // index | (direction and index-only phase bit << 31)
   const double* gab;
   const int* kab;
+  // energy-only mode: visit only alpha strings of the state, gather only the
+  // diagonal entries sigma_D (into sig_out[gorig[D]] when sig_out is given)
+  int energy_only;
+  double* sig_out;
+  const uint32_t* gorig;
 };
 
 struct GroupArgs {
@@ -145,6 +150,7 @@ struct GroupArgs {
   uint64_t* gkey;
   double* gamp;
   uint32_t* grank;
+  uint32_t* gorig;  // original state index of each grouped determinant
   const uint32_t* rank_tab;
   int ks;
   double* acc;  // acc[1] += sum c^2

@@ -399,6 +399,7 @@ row_sweep_kernel(RowArgs A) {
       }
     }
     __syncthreads();
+    if (A.energy_only && sh.gx_cnt == 0) continue;  // same decision in every CTA of the cluster
     // candidates c = 0 .. ns+nd-1 (alpha singles then doubles of X); this CTA takes c = crank (mod gsz)
     for (int cc = threadIdx.x; crank + cc * gsz < ns + nd; cc += kRowThreads) {
       const int c = crank + cc * gsz;
@@ -444,7 +445,16 @@ row_sweep_kernel(RowArgs A) {
 
     row_phase<kRowThreads, true>(A, sh, dy, row, crank, gsz, e_acc);
     cl.sync();
-    row_phase<kRowThreads, false>(A, sh, dy, row, crank, gsz, e_acc);
+    if (A.energy_only) {  // sigma_D of the determinants of X's own group
+      for (long long t = (long long)crank * kRowThreads + threadIdx.x; t < sh.gx_cnt; t += (long long)gsz * kRowThreads) {
+        const long long di = sh.gx_off + t;
+        const double sg = row[A.grank[di]];
+        e_acc += A.gamp[di] * sg;
+        if (A.sig_out) A.sig_out[A.gorig[di]] = sg;
+      }
+    } else {
+      row_phase<kRowThreads, false>(A, sh, dy, row, crank, gsz, e_acc);
+    }
     cl.sync();
     if (dy.touched) {  // clear the entries this CTA touched (others clear theirs)
       for (int w = threadIdx.x; w < nwords; w += kRowThreads) {
@@ -542,7 +552,8 @@ __global__ void group_scan_kernel(const long long* gcount, const unsigned long l
 
 __global__ void group_scatter_kernel(const uint64_t* keys, const double* amps, const long long* n_ptr,
                                      const uint32_t* gid_of, const long long* goff, long long* gfill,
-                                     uint64_t* gkey, double* gamp, uint32_t* grank, const uint32_t* rank_tab, int ks) {
+                                     uint64_t* gkey, double* gamp, uint32_t* grank, uint32_t* gorig,
+                                     const uint32_t* rank_tab, int ks) {
   const long long n = *n_ptr;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const uint32_t g = gid_of[i];
@@ -551,6 +562,7 @@ __global__ void group_scatter_kernel(const uint64_t* keys, const double* amps, c
     gkey[pos] = d;
     gamp[pos] = amps[i];
     grank[pos] = str_rank(rank_tab, ks, even_bits(d >> 1));
+    gorig[pos] = (uint32_t)i;
   }
 }
 
@@ -660,7 +672,7 @@ cudaError_t launch_group_state(const GroupArgs& g, cudaStream_t st) {
   group_count_kernel<<<nb, 256, 0, st>>>(g.keys, g.n, g.atab, g.amask, g.gid_of, g.gcount);
   group_scan_kernel<<<1, 1024, 0, st>>>(g.gcount, g.n_groups, g.goff);
   group_scatter_kernel<<<nb, 256, 0, st>>>(g.keys, g.amps, g.n, g.gid_of, g.goff, g.gfill, g.gkey, g.gamp, g.grank,
-                                           g.rank_tab, g.ks);
+                                           g.gorig, g.rank_tab, g.ks);
   return cudaGetLastError();
 }
 

@@ -115,6 +115,20 @@ def test_sweep_paths_match_oracle(S, sweep, cluster, threads, occ, n_so, n_e, n_
     assert abs(e - eo) < TOL and abs(n2 - n2o) < 1e-13
 
 
+@pytest.mark.parametrize("n_so,n_e,n_ops,seed,n_keep", [(16, 6, 40, 102, 150), (28, 8, 60, 104, 3000),
+                                                        (12, 4, 10, 1, 0)])
+def test_energy_paths_match_oracle(S, n_so, n_e, n_ops, seed, n_keep):
+    """Energy through the alpha-string rows and through the probe kernel."""
+    w = I.small_case(n_so, n_e, n_ops, seed, n_keep=n_keep)
+    c = ctx_for(S, w)
+    c.apply_ansatz(w.ops, w.theta, n_keep)
+    eo, n2o = O.energy(w.n_so, w.h, w.g, *O.apply_ansatz(w.n_so, w.n_e, w.ops, w.theta, n_keep))
+    for mode in (1, 2):
+        c.set_option("energy", mode)
+        e, n2 = c.energy()
+        assert abs(e - eo) < TOL and abs(n2 - n2o) < 1e-13
+
+
 def test_truncation_with_ties_and_zeros(S):
     w = I.small_case(20, 6, 1, 7)
     c = ctx_for(S, w)
