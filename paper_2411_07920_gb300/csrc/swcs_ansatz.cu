@@ -207,19 +207,22 @@ ansatz_kernel(AnsatzArgs a) {
         for (int t = threadIdx.x; t < 256; t += blockDim.x)
           if (s_hist[t]) atomicAdd(&gh[t], s_hist[t]);
         if (!grid_barrier(a.bar, nblocks, a.err, a.timeout_ns)) return;
+        // the whole block pulls the 256 global bins (past the barrier, from L2) into shared memory
+        for (int t = threadIdx.x; t < 256; t += blockDim.x) s_hist[t] = __ldcg(&gh[t]);
+        __syncthreads();
         if (threadIdx.x == 0) {
           long long need = sel.need, cum = 0;
           int chosen = -1;
           long long cnt = 0;
           if (!keyphase) {
             for (int v = 255; v >= 0; --v) {
-              const long long h = (long long)ld_acquire_u32(&gh[v]);
+              const long long h = (long long)s_hist[v];
               if (cum + h >= need) { chosen = v; cnt = h; break; }
               cum += h;
             }
           } else {
             for (int v = 0; v < 256; ++v) {
-              const long long h = (long long)ld_acquire_u32(&gh[v]);
+              const long long h = (long long)s_hist[v];
               if (cum + h >= need) { chosen = v; cnt = h; break; }
               cum += h;
             }

@@ -9,7 +9,7 @@
 
 namespace swcs {
 
-constexpr int kAnsatzThreads = 256;
+constexpr int kAnsatzThreads = 1024;
 constexpr int kSigmaThreads = 256;
 constexpr int kMaxSpin = 32;  // spin-orbitals of one spin (n_so <= 64)
 
