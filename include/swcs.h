@@ -152,6 +152,13 @@ int swcs_stats(swcs_ctx* ctx, int64_t* h_out8);
  *              looked up in the state's index), 2 rows
  *   "row_occupancy" resident 512-thread CTAs per SM the row sweep is compiled
  *              for: 3 (default, register-capped) or 2
+ *   "wait_timeout_ms"  bound of every device-side wait (default 2000)
+ *   "ext_capacity"  hashed sweep: capacity of its first external table (0,
+ *              default: from an estimate); a too-small table is regrown
+ *   "test_skip_arrive"  test hook: the given CTA of the gate kernel leaves
+ *              before its first grid barrier so the others' bounded waits
+ *              run out (-1, default: off); the call then returns
+ *              SWCS_ERR_TIMEOUT and the context stays usable
  *   "gate_blocks"   CTAs of the persistent gate kernel (0, default: whole device)
  *   "row_clusters"  clusters of the row sweep (0, default: as many as fit)
  *   "rows_l2"  1: cap the row sweep's concurrent rows to about half of L2;

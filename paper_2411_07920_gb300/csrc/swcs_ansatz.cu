@@ -95,6 +95,9 @@ ansatz_kernel(AnsatzArgs a) {
     a.tab[1][i].key = kEmpty;
   }
   for (size_t i = gtid; i < 3 * kCtrN; i += gstride) a.ctr[i] = 0;
+  // test hook: the named CTA leaves without arriving, so every other CTA's
+  // bounded wait runs out and the kernel reports kDevTimeout
+  if ((int)blockIdx.x == a.skip_arrive_block) return;
   if (!grid_barrier(a.bar, nblocks, a.err, a.timeout_ns)) return;
   for (size_t i = gtid; i < (size_t)n; i += gstride) {
     if (!idx_insert(a.tab[tab_cur], a.tab_mask, keysA[i], i)) set_error(a.err, kDevTableFull);

@@ -64,6 +64,9 @@ struct swcs_ctx {
   int opt_threads = 512;  // threads per CTA of the row sweep
   int opt_row_occ = 3;    // resident 512-thread CTAs per SM asked of the compiler (2 or 3)
   int opt_energy = 0;     // energy: 0 automatic, 1 probe kernel, 2 alpha-string rows
+  uint64_t opt_timeout_ns = kTimeoutNs;  // bound of every device-side wait
+  int opt_skip_arrive = -1;              // test hook (see swcs_set_option)
+  uint64_t opt_ext_cap = 0;              // hashed sweep: first table capacity (0: sized from an estimate)
   int opt_gate_blocks = 0;   // CTAs of the gate kernel (0: whole device)
   int opt_row_clusters = 0;  // clusters of the row sweep (0: as many as fit)
 
@@ -369,7 +372,8 @@ int run_gates(swcs_ctx* c, const uint8_t* d_ops, const double* d_cs, int n_ops, 
   a.hist = k->hist;
   a.bar = &k->bar;
   a.err = &k->err;
-  a.timeout_ns = kTimeoutNs;
+  a.timeout_ns = c->opt_timeout_ns;
+  a.skip_arrive_block = c->opt_skip_arrive;
   a.snap_keys = snap_keys;
   a.snap_amps = snap_amps;
   a.snap_n = snap_n;
@@ -580,6 +584,11 @@ int sweep(swcs_ctx* c, double* d_g, const uint32_t* sel = nullptr) {
   for (int attempt = 0; attempt < 8; ++attempt) {
     const double per_bucket = est / (double)(1u << lb);
     uint64_t cap = pow2_at_least((uint64_t)std::max(1024.0, per_bucket / load));
+    if (attempt == 0 && c->opt_ext_cap) {
+      cap = pow2_at_least(c->opt_ext_cap);
+      est = std::min(est, 0.5 * load * (double)cap);
+      lb = 0;
+    }
     cap = std::min(cap, cmax);
     if (c->ext_cap < cap) {
       release(c->ext);
@@ -587,7 +596,8 @@ int sweep(swcs_ctx* c, double* d_g, const uint32_t* sel = nullptr) {
       if (r) return r;
       c->ext_cap = cap;
     }
-    cap = std::min<uint64_t>(c->ext_cap, pow2_at_least((uint64_t)std::max(1024.0, per_bucket / load)));
+    if (!(attempt == 0 && c->opt_ext_cap))
+      cap = std::min<uint64_t>(c->ext_cap, pow2_at_least((uint64_t)std::max(1024.0, per_bucket / load)));
     cap = std::min(cap, c->ext_cap);
     CK(cudaMemsetAsync(d_g, 0, sizeof(double) * c->pool_size, c->st));
     CK(cudaMemsetAsync(k->acc, 0, sizeof(double) * 2, c->st));
@@ -620,7 +630,7 @@ int sweep(swcs_ctx* c, double* d_g, const uint32_t* sel = nullptr) {
       CK(launch_k(c, kKGather, [&] { return launch_pool_gather(H, S, T, d_g, k->acc, b == 0, nblk, c->st); }));
     }
     if (overflow) {
-      est = std::max(est * 2.0, (double)cap);
+      est = std::max(est * 4.0, 2.0 * (double)cap);
       while (est / (double)(1u << lb) > load * (double)cmax && lb < 20) ++lb;
       continue;
     }
@@ -1127,6 +1137,14 @@ int swcs_set_option(swcs_ctx* c, const char* name, int64_t value) {
   } else if (k == "row_clusters") {
     if (value < 0) return fail(c, SWCS_ERR_INVALID_ARG, "row_clusters must be >= 0");
     c->opt_row_clusters = (int)value;
+  } else if (k == "wait_timeout_ms") {
+    if (value < 1 || value > 60000) return fail(c, SWCS_ERR_INVALID_ARG, "wait_timeout_ms must be 1..60000");
+    c->opt_timeout_ns = (uint64_t)value * 1000000ull;
+  } else if (k == "test_skip_arrive") {
+    c->opt_skip_arrive = value < 0 ? -1 : (int)value;
+  } else if (k == "ext_capacity") {
+    if (value < 0) return fail(c, SWCS_ERR_INVALID_ARG, "ext_capacity must be >= 0");
+    c->opt_ext_cap = (uint64_t)value;
   } else if (k == "energy") {
     if (value < 0 || value > 2) return fail(c, SWCS_ERR_INVALID_ARG, "energy must be 0, 1 or 2");
     c->opt_energy = (int)value;

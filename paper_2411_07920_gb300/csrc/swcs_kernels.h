@@ -41,6 +41,7 @@ struct AnsatzArgs {
   long long* snap_n;
   int64_t snap_stride;
   long long* stats;  // optional: [0] gates, [1] select passes, [6] max |Phi|, [7] sum of input sizes
+  int skip_arrive_block;  // test hook: this CTA never arrives at its first grid barrier (-1: off)
 };
 
 int ansatz_blocks_per_sm();
