@@ -240,12 +240,7 @@ def run_swcs(args):
         energy_ms.append(ev0.elapsed_time(ev1))
     ctx.profile_read(reset=True)
     ctx.profile_enable(False)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = t.item()
-    ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1e3)
+    ms_per_step, value = aggregate(total_ms, args.steps, world, dev)
 
     # ------------------------------------------------------------ roofline of the dominant kernel
     import math
@@ -358,6 +353,17 @@ def run_swcs(args):
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def aggregate(total_ms, steps, world, device):
+    """Whole-job throughput: every rank ran `steps` replicas of the workload;
+    the job time is the slowest rank's (max over ranks)."""
+    import torch
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = t.item()
+    return total_ms / steps, world * steps / (total_ms / 1e3)
 
 
 def measured_traffic(kernel):
