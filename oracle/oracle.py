@@ -37,6 +37,8 @@ def _load():
     c_int, c_i64, c_d = ctypes.c_int, ctypes.c_int64, ctypes.c_double
     L.orc_apply_ansatz.argtypes = [c_int, c_int, _u8p, _f64p, c_int, c_i64, _u64p, _f64p, c_i64]
     L.orc_apply_ansatz.restype = c_i64
+    L.orc_apply_ansatz_eps.argtypes = [c_int, c_int, _u8p, _f64p, c_int, c_i64, c_d, _u64p, _f64p, c_i64]
+    L.orc_apply_ansatz_eps.restype = c_i64
     L.orc_gate.argtypes = [_u64p, _f64p, c_i64, _u8p, c_d, c_d, c_i64, _u64p, _f64p, c_i64]
     L.orc_gate.restype = c_i64
     L.orc_truncate.argtypes = [_u64p, _f64p, c_i64, c_i64, _u64p, _f64p, c_i64]
@@ -59,6 +61,9 @@ def _load():
     L.orc_energy_grad.argtypes = [c_int, c_int, _f64p, _f64p, _u8p, _f64p, c_int, c_i64,
                                   ctypes.POINTER(c_d), _f64p]
     L.orc_energy_grad.restype = None
+    L.orc_energy_grad_eps.argtypes = [c_int, c_int, _f64p, _f64p, _u8p, _f64p, c_int, c_i64, c_d,
+                                      ctypes.POINTER(c_d), _f64p]
+    L.orc_energy_grad_eps.restype = None
     L.orc_sigma_at.argtypes = [c_int, _f64p, _f64p, _u64p, _f64p, c_i64, _u64p, c_i64, _f64p]
     L.orc_sigma_at.restype = None
     L.orc_pool_gradients_pull.argtypes = [c_int, _f64p, _f64p, _u64p, _f64p, c_i64, _i64p, c_i64, _f64p]
@@ -75,15 +80,18 @@ def _ham(h, g):
     return _c(h, np.float64).reshape(-1), _c(g, np.float64).reshape(-1)
 
 
-def apply_ansatz(n_so, n_e, ops, theta, n_keep, cap=1 << 22):
-    """State after the gate sequence (Eq. 1), truncated after every gate; sorted by key."""
+def apply_ansatz(n_so, n_e, ops, theta, n_keep, cap=1 << 22, eps=0.0):
+    """State after the gate sequence (Eq. 1), truncated after every gate; sorted by key.
+
+    eps > 0 adds the magnitude criterion of Sec. II.B: |c| < eps is dropped
+    after every gate, before the size criterion (top n_keep)."""
     L = _load()
     ops = _c(ops, np.uint8).reshape(-1)
     theta = _c(theta, np.float64)
     while True:
         k = np.zeros(cap, np.uint64)
         a = np.zeros(cap, np.float64)
-        n = L.orc_apply_ansatz(n_so, n_e, ops, theta, len(theta), int(n_keep), k, a, cap)
+        n = L.orc_apply_ansatz_eps(n_so, n_e, ops, theta, len(theta), int(n_keep), float(eps), k, a, cap)
         if n <= cap:
             return k[:n].copy(), a[:n].copy()
         cap = int(n)
@@ -165,15 +173,16 @@ def pool_gradients_brute(n_so, h, g, keys, amps):
     return out
 
 
-def energy_grad(n_so, n_e, h, g, ops, theta, n_keep):
-    """(E, dE/dtheta) of the truncated circuit with fixed truncation projectors."""
+def energy_grad(n_so, n_e, h, g, ops, theta, n_keep, eps=0.0):
+    """(E, dE/dtheta) of the truncated circuit with fixed truncation projectors
+    (eps: magnitude criterion, as in apply_ansatz)."""
     L = _load()
     hh, gg = _ham(h, g)
     theta = _c(theta, np.float64)
     e = ctypes.c_double()
     d = np.zeros(len(theta))
-    L.orc_energy_grad(n_so, n_e, hh, gg, _c(ops, np.uint8).reshape(-1), theta, len(theta), int(n_keep),
-                      ctypes.byref(e), d)
+    L.orc_energy_grad_eps(n_so, n_e, hh, gg, _c(ops, np.uint8).reshape(-1), theta, len(theta), int(n_keep),
+                          float(eps), ctypes.byref(e), d)
     return e.value, d
 
 

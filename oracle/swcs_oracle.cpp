@@ -156,6 +156,17 @@ State truncate_top(const State& in, int64_t n_keep) {
   return out;
 }
 
+// Truncation after a gate (Sec. II.B): the magnitude criterion first (drop
+// every |c| < eps; eps <= 0 keeps all nonzero amplitudes), then the size
+// criterion (top n_keep of what is left, as truncate_top).
+State truncate(const State& in, int64_t n_keep, double eps) {
+  if (eps <= 0.0) return truncate_top(in, n_keep);
+  State kept;
+  for (const auto& kv : in)
+    if (std::fabs(kv.second) >= eps) kept.insert(kv);
+  return truncate_top(kept, n_keep);
+}
+
 // ---------------------------------------------------------------------------
 // Hamiltonian H = sum h_pq a+_p a_q + 1/4 sum <pq||rs> a+_p a+_q a_s a_r.
 // ---------------------------------------------------------------------------
@@ -328,8 +339,10 @@ extern "C" {
 // ops[0] acting first; truncation to n_keep after every gate (n_keep <= 0:
 // none).  Writes up to cap determinants sorted by bitstring; returns the
 // state size (may exceed cap, then nothing is written).
-int64_t orc_apply_ansatz(int n_so, int n_e, const uint8_t* ops, const double* theta, int n_ops,
-                         int64_t n_keep, uint64_t* keys_out, double* amps_out, int64_t cap) {
+// orc_apply_ansatz_eps also drops |c| < eps after every gate (the magnitude
+// criterion of Sec. II.B), before the size criterion.
+int64_t orc_apply_ansatz_eps(int n_so, int n_e, const uint8_t* ops, const double* theta, int n_ops,
+                             int64_t n_keep, double eps, uint64_t* keys_out, double* amps_out, int64_t cap) {
   (void)n_so;
   State s;
   det_t hf = (n_e >= 64) ? ~0ull : ((1ull << n_e) - 1ull);
@@ -337,7 +350,7 @@ int64_t orc_apply_ansatz(int n_so, int n_e, const uint8_t* ops, const double* th
   for (int k = 0; k < n_ops; ++k) {
     Op o = op_from_bytes(ops + 5 * k);
     s = gate_apply(s, o, std::cos(theta[k]), std::sin(theta[k]));
-    s = truncate_top(s, n_keep);
+    s = truncate(s, n_keep, eps);
   }
   int64_t n = (int64_t)s.size();
   if (n <= cap) {
@@ -345,6 +358,11 @@ int64_t orc_apply_ansatz(int n_so, int n_e, const uint8_t* ops, const double* th
     for (const auto& kv : s) { keys_out[i] = kv.first; amps_out[i] = kv.second; ++i; }
   }
   return n;
+}
+
+int64_t orc_apply_ansatz(int n_so, int n_e, const uint8_t* ops, const double* theta, int n_ops,
+                         int64_t n_keep, uint64_t* keys_out, double* amps_out, int64_t cap) {
+  return orc_apply_ansatz_eps(n_so, n_e, ops, theta, n_ops, n_keep, 0.0, keys_out, amps_out, cap);
 }
 
 // One gate (given cos/sin) and truncation on an arbitrary state.
@@ -467,16 +485,16 @@ void orc_pool_gradients_brute(int n_so, const double* h, const double* g, const 
 // onto the kept set S_g:  psi_g = P_g U_g psi_{g-1},  phi_g = U_g psi_{g-1}.
 //   nu_M = P_M (H - E) psi_M,  nu_{g-1} = P_{g-1} U_g^dag nu_g,
 //   dE/dtheta_g = 2 <nu_g | A_g phi_g> / <psi_M|psi_M>.
-void orc_energy_grad(int n_so, int n_e, const double* h, const double* g, const uint8_t* ops,
-                     const double* theta, int n_ops, int64_t n_keep, double* e_out,
-                     double* dtheta_out) {
+void orc_energy_grad_eps(int n_so, int n_e, const double* h, const double* g, const uint8_t* ops,
+                         const double* theta, int n_ops, int64_t n_keep, double eps, double* e_out,
+                         double* dtheta_out) {
   Ham H{n_so, h, g};
   std::vector<State> psi(n_ops + 1);
   det_t hf = (n_e >= 64) ? ~0ull : ((1ull << n_e) - 1ull);
   psi[0][hf] = 1.0;
   for (int k = 0; k < n_ops; ++k) {
     Op o = op_from_bytes(ops + 5 * k);
-    psi[k + 1] = truncate_top(gate_apply(psi[k], o, std::cos(theta[k]), std::sin(theta[k])), n_keep);
+    psi[k + 1] = truncate(gate_apply(psi[k], o, std::cos(theta[k]), std::sin(theta[k])), n_keep, eps);
   }
   double n2 = 0.0;
   const double e = energy_of(H, psi[n_ops], &n2);
@@ -511,6 +529,12 @@ void orc_energy_grad(int n_so, int n_e, const double* h, const double* g, const 
     }
     nu.swap(proj);
   }
+}
+
+void orc_energy_grad(int n_so, int n_e, const double* h, const double* g, const uint8_t* ops,
+                     const double* theta, int n_ops, int64_t n_keep, double* e_out,
+                     double* dtheta_out) {
+  orc_energy_grad_eps(n_so, n_e, h, g, ops, theta, n_ops, n_keep, 0.0, e_out, dtheta_out);
 }
 
 // sigma_E = sum_{D in S} <E|H|D> c_D at arbitrary determinants E, each

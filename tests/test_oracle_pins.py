@@ -330,3 +330,71 @@ def test_pull_routes_match_push_routes():
     hp = H @ psi
     pick = basis[::5].astype(np.uint64)
     assert np.abs(O.sigma_at(w.n_so, w.h, w.g, k, a, pick) - hp[::5]).max() < 1e-12
+
+
+# ---------------------------------------------------------------- magnitude truncation
+@pytest.mark.parametrize("eps,n_keep", [(2e-3, 0), (2e-3, 25), (2e-2, 0)])
+def test_magnitude_truncated_circuit_matches_statevector(eps, n_keep):
+    """Sec. II.B's magnitude criterion: after every gate the dense statevector
+    (expm_multiply of Eq. 2) loses every |c| < eps, then keeps the top n_keep."""
+    w = I.small_case(12, 4, 14, 33)
+    a_ops = J.annihilators(w.n_so)
+    psi = np.zeros(1 << w.n_so)
+    psi[(1 << w.n_e) - 1] = 1.0
+    dropped = 0
+    for op, th in zip(w.ops, w.theta):
+        psi = spla.expm_multiply(th * J.kappa_matrix(a_ops, op), psi)
+        idx = np.flatnonzero(np.abs(psi) >= eps).astype(np.uint64)
+        dropped += int(np.count_nonzero(np.abs(psi) > 1e-12)) - len(idx)
+        kk, aa = _lex_top(idx, psi[idx.astype(np.int64)], n_keep)
+        psi = _dense(kk, aa, w.n_so)
+    k, a = O.apply_ansatz(w.n_so, w.n_e, w.ops, w.theta, n_keep, eps=eps)
+    assert dropped > 0  # the criterion acted
+    assert np.abs(_dense(k, a, w.n_so) - psi).max() < 1e-13
+    assert np.abs(a).min() >= eps
+
+
+def test_magnitude_truncation_acts_after_every_gate():
+    """The same single excitation twice: exp(t2 k) exp(t1 k) = exp((t1+t2) k)
+    without truncation; with eps between |sin t1| and |cos t1| the excited
+    determinant is dropped after the first gate, so the second gate starts
+    again from the reference alone (amplitudes cos t1 cos t2, +-cos t1 sin t2)."""
+    n_so, n_e = 8, 2
+    op = np.array([1, 0, 2, 0, 0], np.uint8)  # tau = a+_2 a_0
+    t1, t2 = 0.05, 0.7
+    ops = np.stack([op, op])
+    k0, a0 = O.apply_ansatz(n_so, n_e, ops, np.array([t1, t2]), 0)
+    assert np.allclose(sorted(np.abs(a0)), sorted([abs(math.cos(t1 + t2)), abs(math.sin(t1 + t2))]), atol=1e-15)
+    k, a = O.apply_ansatz(n_so, n_e, ops, np.array([t1, t2]), 0, eps=0.1)
+    assert sorted(np.abs(a)) == pytest.approx(sorted([math.cos(t1) * math.sin(t2), math.cos(t1) * math.cos(t2)]),
+                                              abs=1e-15)
+    assert set(k.tolist()) == {0b11, 0b110}
+
+
+def test_magnitude_truncated_adjoint_matches_finite_differences():
+    w = I.small_case(12, 4, 12, 63)
+    eps = 5e-3
+    e, d = O.energy_grad(w.n_so, w.n_e, w.h, w.g, w.ops, w.theta, 0, eps=eps)
+    M = len(w.ops)
+
+    def kept_sets(theta):
+        return [O.apply_ansatz(w.n_so, w.n_e, w.ops[:m], theta[:m], 0, eps=eps)[0] for m in range(1, M + 1)]
+
+    sets0 = kept_sets(w.theta)
+    hstep = 1e-5
+    checked = 0
+    for g in range(M):
+        tp, tm = w.theta.copy(), w.theta.copy()
+        tp[g] += hstep
+        tm[g] -= hstep
+        if not (all(np.array_equal(x, y) for x, y in zip(kept_sets(tp), sets0)) and
+                all(np.array_equal(x, y) for x, y in zip(kept_sets(tm), sets0))):
+            continue
+        kp, ap = O.apply_ansatz(w.n_so, w.n_e, w.ops, tp, 0, eps=eps)
+        km, am = O.apply_ansatz(w.n_so, w.n_e, w.ops, tm, 0, eps=eps)
+        fd = (O.energy(w.n_so, w.h, w.g, kp, ap)[0] - O.energy(w.n_so, w.h, w.g, km, am)[0]) / (2 * hstep)
+        assert abs(fd - d[g]) < 1e-7
+        checked += 1
+    assert checked >= M // 2
+    # the criterion dropped determinants on this circuit
+    assert len(O.apply_ansatz(w.n_so, w.n_e, w.ops, w.theta, 0)[0]) > len(sets0[-1])
