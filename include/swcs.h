@@ -98,6 +98,16 @@ int swcs_apply_gates(swcs_ctx* ctx, const uint8_t* h_ops, const double* h_theta,
 /* Truncate the current state alone (same rule as after a gate). */
 int swcs_truncate(swcs_ctx* ctx, int64_t n_keep);
 
+/* Magnitude criterion of the truncation (Sec. II.B, the alternative to a
+ * fixed determinant count): from now on every truncation of this context
+ * (after each gate of swcs_apply_ansatz / swcs_apply_gates / swcs_truncate,
+ * and in the forward replays of swcs_energy_grad, whose projectors are the
+ * kept sets) first drops every determinant with |c| < eps, then keeps the
+ * n_keep largest of the rest (n_keep <= 0: all of them; n_keep also bounds
+ * the memory).  eps = 0 (the default) restores the count-only rule.
+ * SWCS_ERR_INVALID_ARG for a negative or non-finite eps. */
+int swcs_set_truncation_threshold(swcs_ctx* ctx, double eps);
+
 /* E = <psi|H|psi>/<psi|psi> and <psi|psi> of the current state. */
 int swcs_energy(swcs_ctx* ctx, double* h_e_out, double* h_norm2_out);
 /* Device variant: d_out[0] = E, d_out[1] = <psi|psi>. */

@@ -14,8 +14,9 @@
 // at most two separately rounded products, so the result does not depend on
 // the order of work: bit-identical to any correct sequential evaluation.
 //
-// Truncation: keep the n_keep largest |c|, ties at the cut by smaller
-// bitstring.  |c| as an IEEE-754 bit pattern with the sign cleared orders
+// Truncation: entries below the magnitude threshold (or exactly zero) are
+// dropped, then the n_keep largest |c| of the rest are kept, ties at the cut
+// by smaller bitstring.  |c| as an IEEE-754 bit pattern with the sign cleared orders
 // like the value, so an MSD radix select over 8-bit digits (first digit 7
 // bits) finds the cut; when the cut lands on several equal |c| a second
 // radix select over the bitstrings of the tied entries picks the smallest.
@@ -50,9 +51,9 @@ struct SelState {
   int pass;                    // passes run
 };
 
-__device__ __forceinline__ bool keep_entry(const SelState& s, uint64_t key, double c) {
+__device__ __forceinline__ bool keep_entry(const SelState& s, uint64_t key, double c, uint64_t min_bits) {
   const uint64_t x = abs_bits(c);
-  if (x == 0) return false;
+  if (x < min_bits) return false;
   if (s.mode == 0) return true;
   if (s.mode == 1) return (x >> s.shift) >= (s.prefix >> s.shift);
   if (x != s.prefix) return x > s.prefix;
@@ -142,7 +143,7 @@ ansatz_kernel(AnsatzArgs a) {
             out = t1;
             const double t = __dmul_rn(c, sn);
             extra = up ? apply_sign(t, sbit) : apply_sign(t, !sbit);
-            has_extra = (extra != 0.0);
+            has_extra = abs_bits(extra) >= a.min_abs_bits;
           }
         } else {
           out = c;
@@ -160,7 +161,7 @@ ansatz_kernel(AnsatzArgs a) {
           set_error(a.err, kDevTableFull);
         }
       }
-      const bool zero = live && out == 0.0;
+      const bool zero = live && abs_bits(out) < a.min_abs_bits;  // dropped: zero or below threshold
       const unsigned zb = __ballot_sync(__activemask(), zero);
       if ((threadIdx.x & 31) == 0 && zb) atomicAdd(&ctr[kCtrZero], (unsigned long long)__popc(zb));
     }
@@ -192,7 +193,7 @@ ansatz_kernel(AnsatzArgs a) {
         for (size_t i = gtid; i < (size_t)m; i += gstride) {
           const double c = ampsB[i];
           const uint64_t x = abs_bits(c);
-          if (x == 0) continue;
+          if (x < a.min_abs_bits) continue;
           uint64_t v;
           if (!keyphase) {
             if (p > 0 && (x >> (sh + 8)) != (pre >> (sh + 8))) continue;
@@ -266,7 +267,7 @@ ansatz_kernel(AnsatzArgs a) {
       if (i < (size_t)m) {
         k = keysB[i];
         c = ampsB[i];
-        keep = keep_entry(s, k, c);
+        keep = keep_entry(s, k, c, a.min_abs_bits);
       }
       const unsigned long long pos = warp_alloc(&ctr[kCtrKept], keep);
       if (keep) {

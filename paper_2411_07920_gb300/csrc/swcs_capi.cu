@@ -63,6 +63,7 @@ struct swcs_ctx {
   int opt_rows_l2 = 0;  // cap concurrent rows to about half of L2
   int opt_threads = 512;  // threads per CTA of the row sweep
   int opt_row_occ = 3;    // resident 512-thread CTAs per SM asked of the compiler (2 or 3)
+  double trunc_eps = 0.0;  // magnitude criterion of the truncation (0: off)
   int opt_energy = 0;     // energy: 0 automatic, 1 probe kernel, 2 alpha-string rows
   uint64_t opt_timeout_ns = kTimeoutNs;  // bound of every device-side wait
   int opt_skip_arrive = -1;              // test hook (see swcs_set_option)
@@ -363,6 +364,11 @@ int run_gates(swcs_ctx* c, const uint8_t* d_ops, const double* d_cs, int n_ops, 
   a.cs = d_cs;
   a.n_ops = n_ops;
   a.n_keep = n_keep;
+  {  // |c| >= eps <=> abs bit pattern >= eps's bit pattern (IEEE-754 order of non-negative doubles)
+    uint64_t eb = 0;
+    std::memcpy(&eb, &c->trunc_eps, 8);
+    a.min_abs_bits = (c->trunc_eps > 0.0) ? eb : 1ull;
+  }
   a.reset_to_hf = reset ? 1 : 0;
   a.hf = (c->ne >= 64) ? ~0ull : ((1ull << c->ne) - 1ull);
   Ctrl* k = ctrl(c);
@@ -410,6 +416,20 @@ int64_t host_state_size(swcs_ctx* c) {
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return -1;
   c->n_state_host = ns;
   return ns;
+}
+
+// Energies and sweeps need at least one determinant.  A state can be empty
+// after swcs_set_state with no nonzero amplitude, or after the magnitude
+// criterion removed every determinant (count-only truncation keeps the norm).
+// The size is read back (one synchronisation) unless already known; the
+// sweeps read it anyway to size their launches.
+int need_nonempty(swcs_ctx* c) {
+  int r = need_state(c);
+  if (r) return r;
+  const int64_t n = host_state_size(c);
+  if (n < 0) return fail(c, SWCS_ERR_CUDA, "cannot read state size");
+  if (n == 0) return fail(c, SWCS_ERR_INVALID_ARG, "the state is empty (no determinant with a kept amplitude)");
+  return SWCS_OK;
 }
 
 int upload_ops(swcs_ctx* c, const uint8_t* h_ops, const double* h_theta, int n_ops) {
@@ -901,7 +921,7 @@ int swcs_truncate(swcs_ctx* c, int64_t n_keep) {
 }
 
 int swcs_energy_dev(swcs_ctx* c, double* d_out) {
-  int r = need_state(c);
+  int r = need_nonempty(c);
   if (r) return r;
   Ctrl* k = ctrl(c);
   if ((r = energy_rows(c, nullptr)) != 1) {
@@ -927,7 +947,7 @@ int swcs_energy(swcs_ctx* c, double* e_out, double* n2_out) {
 }
 
 int swcs_pool_gradients_dev(swcs_ctx* c, double* d_g_out, const int64_t* d_subset, int64_t n_subset) {
-  int r = need_state(c);
+  int r = need_nonempty(c);
   if (r) return r;
   if (!d_g_out) return fail(c, SWCS_ERR_INVALID_ARG, "null output");
   double* g = d_g_out;
@@ -945,7 +965,7 @@ int swcs_pool_gradients_dev(swcs_ctx* c, double* d_g_out, const int64_t* d_subse
 }
 
 int swcs_pool_gradients(swcs_ctx* c, double* h_g_out, const int64_t* h_subset, int64_t n_subset) {
-  int r = need_state(c);
+  int r = need_nonempty(c);
   if (r) return r;
   if (!h_g_out) return fail(c, SWCS_ERR_INVALID_ARG, "null output");
   if ((r = ensure(c, c->gdev, sizeof(double) * c->pool_size))) return r;
@@ -980,7 +1000,7 @@ int swcs_get_state(swcs_ctx* c, uint64_t* keys, double* amps, int64_t cap, int64
   const int64_t n = host_state_size(c);
   if (n < 0) return fail(c, SWCS_ERR_CUDA, "cannot read state size");
   if (n_out) *n_out = n;
-  if (cap < n) return SWCS_OK;
+  if (cap < n || n == 0) return SWCS_OK;
   std::vector<uint64_t> k(n);
   std::vector<double> a(n);
   CK(cudaMemcpy(k.data(), c->keys_a.p, 8 * n, cudaMemcpyDeviceToHost));
@@ -1022,8 +1042,10 @@ int swcs_set_state(swcs_ctx* c, const uint64_t* keys, const double* amps, int64_
   const int64_t m = (int64_t)k.size();
   c->have_state = false;
   if ((r = ensure_state_buffers(c, std::max<int64_t>(m, 1)))) return r;
-  CK(cudaMemcpyAsync(c->keys_a.p, k.data(), 8 * m, cudaMemcpyHostToDevice, c->st));
-  CK(cudaMemcpyAsync(c->amps_a.p, a.data(), 8 * m, cudaMemcpyHostToDevice, c->st));
+  if (m > 0) {
+    CK(cudaMemcpyAsync(c->keys_a.p, k.data(), 8 * m, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->amps_a.p, a.data(), 8 * m, cudaMemcpyHostToDevice, c->st));
+  }
   long long mm = m;
   CK(cudaMemcpyAsync(&ctrl(c)->n_state, &mm, 8, cudaMemcpyHostToDevice, c->st));
   CK(cudaStreamSynchronize(c->st));
@@ -1053,7 +1075,7 @@ int swcs_stats(swcs_ctx* c, int64_t* out8) {
 }
 
 int swcs_sweep_energy(swcs_ctx* c, double* e_out, double* n2_out) {
-  int r = need_state(c);
+  int r = need_nonempty(c);
   if (r) return r;
   double out[2];
   CK(cudaMemcpyAsync(out, ctrl(c)->eout, 16, cudaMemcpyDeviceToHost, c->st));
@@ -1064,7 +1086,7 @@ int swcs_sweep_energy(swcs_ctx* c, double* e_out, double* n2_out) {
 }
 
 int swcs_get_sigma(swcs_ctx* c, uint64_t* keys, double* sigma, int64_t cap, int64_t* n_out) {
-  int r = need_state(c);
+  int r = need_nonempty(c);
   if (r) return r;
   const int64_t n = host_state_size(c);
   if (n < 0) return fail(c, SWCS_ERR_CUDA, "cannot read state size");
@@ -1092,7 +1114,7 @@ int swcs_get_sigma(swcs_ctx* c, uint64_t* keys, double* sigma, int64_t cap, int6
 }
 
 int swcs_pool_features_dev(swcs_ctx* c, uint16_t* d_x) {
-  int r = need_state(c);
+  int r = need_nonempty(c);
   if (r) return r;
   if (!d_x) return fail(c, SWCS_ERR_INVALID_ARG, "null output");
   if ((r = ensure(c, c->occ, 64 * sizeof(double)))) return r;
@@ -1105,7 +1127,7 @@ int swcs_pool_features_dev(swcs_ctx* c, uint16_t* d_x) {
 }
 
 int swcs_pool_screen_dev(swcs_ctx* c, swcs_mlp* m, double frac, int64_t* d_subset, int64_t* h_n_subset) {
-  int r = need_state(c);
+  int r = need_nonempty(c);
   if (r) return r;
   if (!m || !d_subset || !(frac > 0.0) || frac > 1.0) return fail(c, SWCS_ERR_INVALID_ARG, "bad screening arguments");
   const int64_t P = c->pool_size;
@@ -1122,6 +1144,13 @@ int swcs_pool_screen_dev(swcs_ctx* c, swcs_mlp* m, double frac, int64_t* d_subse
   }));
   c->launches += 4;
   if (h_n_subset) *h_n_subset = k;
+  return SWCS_OK;
+}
+
+int swcs_set_truncation_threshold(swcs_ctx* c, double eps) {
+  if (!c) return SWCS_ERR_INVALID_ARG;
+  if (!(eps >= 0.0) || !std::isfinite(eps)) return fail(c, SWCS_ERR_INVALID_ARG, "threshold must be finite and >= 0");
+  c->trunc_eps = eps;
   return SWCS_OK;
 }
 
@@ -1256,6 +1285,8 @@ int swcs_energy_grad(swcs_ctx* c, const uint8_t* h_ops, const double* h_theta, i
     if ((r = run_gates(c, dops + 5 * g0, dcs + 2 * g0, g1 - g0, n_keep, seg == 0))) return r;
   }
   if ((r = save_slot(ncp))) return r;
+  c->have_state = true;
+  if ((r = need_nonempty(c))) return r;
   // ---- energy, sigma and nu_M = P_M (H - E) psi_M on the final state
   CK(cudaMemsetAsync(k->acc, 0, 16, c->st));
   const int nblk = c->nsm * sigma_blocks_per_sm();

@@ -25,7 +25,8 @@ struct AnsatzArgs {
   const uint8_t* ops;  // 5 bytes per gate
   const double* cs;    // (cos theta, sin theta) per gate
   int n_ops;
-  int64_t n_keep;      // <= 0: no truncation
+  int64_t n_keep;      // <= 0: no size criterion
+  uint64_t min_abs_bits;  // magnitude criterion: |c| bit patterns below this are dropped (1: exact zeros only)
   int reset_to_hf;
   uint64_t hf;
   long long* n_state;  // in: input size (unless reset_to_hf); out: output size

@@ -44,6 +44,7 @@ _SIGS = {
     "swcs_apply_ansatz_dev": ([_vp, _vp, _vp, _i, _i64], _i),
     "swcs_apply_gates": ([_vp, _vp, _vp, _i, _i64], _i),
     "swcs_truncate": ([_vp, _i64], _i),
+    "swcs_set_truncation_threshold": ([_vp, ctypes.c_double], _i),
     "swcs_energy": ([_vp, _pd, _pd], _i),
     "swcs_energy_dev": ([_vp, _vp], _i),
     "swcs_pool_gradients": ([_vp, _vp, _vp, _i64], _i),
@@ -334,6 +335,11 @@ class Context:
 
     def truncate(self, n_keep):
         self._ck(lib.swcs_truncate(self._h, int(n_keep)))
+
+    def set_truncation_threshold(self, eps):
+        """Magnitude criterion (drop |c| < eps before the size criterion) for
+        every later truncation of this context; 0 turns it off."""
+        self._ck(lib.swcs_set_truncation_threshold(self._h, float(eps)))
 
     def energy(self):
         e, n2 = ctypes.c_double(), ctypes.c_double()
