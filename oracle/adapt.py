@@ -1,0 +1,118 @@
+"""CPU oracle of the ADAPT-VQE outer loop (Sec. II.C, Fig. 1) and of the
+BFGS-2 / BFGS-2F bootstrap procedures (Sec. IV.D) — test infrastructure only.
+
+The loop, step by step as Fig. 1 orders it, on top of the oracle's SWCS:
+  step 3  the reference determinant, empty ansatz;
+  step 4  the pool gradient: g_k for every generalized single and double
+          appended to the end of the current (truncated) ansatz;
+  step 5  converged when ||g|| < eps;
+  step 6  append the operator with the largest |g_k|, its parameter 0
+          (reading: values within a relative 1e-9 of the largest count as
+          equal, and the first of them in canonical pool order is taken);
+  step 7  VQE: BFGS over all parameters, energy and gradient of the
+          truncated circuit from the oracle's adjoint.
+BFGS-2 replaces step 7 by (1) BFGS over the new parameter alone, the others
+frozen at their previous optimum, then (2) BFGS over all of them; BFGS-2F
+keeps (1) only.  A bootstrap runs ADAPT with a first N_CUT and continues the
+same ansatz with larger N_CUT values, one stage after the other.
+
+The optimiser is SciPy's BFGS (the one of Sec. III), used as a library
+primitive; its convergence threshold is the gradient norm `gtol` (1e-6 in
+Sec. III).
+
+Parity status: pinned by tests/test_adapt_oracle.py — the first iteration
+against the 2x2 eigenproblem of the reference and the chosen excitation
+(dense Jordan-Wigner Hamiltonian), the BFGS-2 first step against the
+closed-form minimum of a + b cos 2t + c sin 2t, the variational bound and
+monotone energies against dense FCI, frozen parameters under BFGS-2F.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.optimize as so
+
+from . import oracle as O
+
+
+def _largest(g, rel=1e-9):
+    mag = np.abs(np.asarray(g, np.float64))
+    top = mag.max()
+    for k in range(len(mag)):
+        if mag[k] >= top * (1.0 - rel):
+            return k
+    return int(np.argmax(mag))
+
+
+class OracleAdapt:
+    """ADAPT-VQE state: Hamiltonian, pool, ansatz so far, N_CUT."""
+
+    def __init__(self, n_so, n_e, h, g, n_keep, eps=1e-2, gtol=1e-6):
+        self.n_so, self.n_e, self.h, self.g = n_so, n_e, h, g
+        self.n_keep = n_keep
+        self.eps, self.gtol = eps, gtol
+        self.pool = O.pool_ops(n_so)
+        self.ops = np.zeros((0, 5), np.uint8)
+        self.theta = np.zeros(0)
+        self.chosen = []
+        self.energies = []
+        self.grad_norms = []
+        self.calls = 0
+
+    def _eg(self, theta):
+        self.calls += 1
+        return O.energy_grad(self.n_so, self.n_e, self.h, self.g, self.ops, theta, self.n_keep)
+
+    def pool_gradient(self):
+        keys, amps = O.apply_ansatz(self.n_so, self.n_e, self.ops, self.theta, self.n_keep)
+        return O.pool_gradients(self.n_so, self.h, self.g, keys, amps)
+
+    def _bfgs_all(self, theta):
+        r = so.minimize(self._eg, theta, jac=True, method="BFGS", options={"gtol": self.gtol})
+        return np.asarray(r.x, np.float64)
+
+    def _bfgs_last(self, theta):
+        head = theta[:-1].copy()
+
+        def f(t):
+            e, d = self._eg(np.concatenate([head, t]))
+            return e, d[-1:]
+        r = so.minimize(f, theta[-1:], jac=True, method="BFGS", options={"gtol": self.gtol})
+        return np.concatenate([head, np.asarray(r.x, np.float64)])
+
+    def iterate(self, mode="bfgs"):
+        """One pass of steps 4-7; returns False once converged (step 5)."""
+        g = self.pool_gradient()
+        norm = float(np.sqrt(np.sum(g * g)))
+        self.grad_norms.append(norm)
+        if norm < self.eps:
+            return False
+        k = _largest(g)
+        self.chosen.append(k)
+        self.ops = np.concatenate([self.ops, self.pool[k][None, :]])
+        theta = np.concatenate([self.theta, [0.0]])
+        if mode in ("bfgs2", "bfgs2f"):
+            theta = self._bfgs_last(theta)
+        if mode in ("bfgs", "bfgs2"):
+            theta = self._bfgs_all(theta)
+        self.theta = theta
+        keys, amps = O.apply_ansatz(self.n_so, self.n_e, self.ops, theta, self.n_keep)
+        self.energies.append(O.energy(self.n_so, self.h, self.g, keys, amps)[0])
+        return True
+
+    def run(self, max_iter, mode="bfgs"):
+        for _ in range(max_iter):
+            if not self.iterate(mode):
+                return True
+        return False
+
+
+def bootstrap(n_so, n_e, h, g, schedule, max_iter, eps=1e-2, gtol=1e-6, first="bfgs2", then="bfgs2f"):
+    """ADAPT with N_CUT = schedule[0] (optimiser `first`), continued with
+    schedule[1:] (optimiser `then`), at most max_iter iterations per stage."""
+    a = OracleAdapt(n_so, n_e, h, g, schedule[0], eps, gtol)
+    stages = []
+    for i, n_keep in enumerate(schedule):
+        a.n_keep = n_keep
+        conv = a.run(max_iter, first if i == 0 else then)
+        stages.append(dict(n_keep=n_keep, n_params=len(a.theta), converged=conv))
+    return a, stages

@@ -119,7 +119,7 @@ void drop_zeros(State& s) {
 // exp(theta kappa) D' = cos D' - s sin D.  Determinants outside every block
 // are left unchanged.  Each output receives at most two products, summed in
 // the merge map.
-State gate_apply(const State& in, const Op& o, double c, double sn) {
+State gate_apply(const State& in, const Op& o, double c, double sn, bool keep_zeros = false) {
   State out;
   for (const auto& kv : in) {
     const det_t d = kv.first;
@@ -138,7 +138,7 @@ State gate_apply(const State& in, const Op& o, double c, double sn) {
       out[d] += amp;
     }
   }
-  drop_zeros(out);
+  if (!keep_zeros) drop_zeros(out);
   return out;
 }
 
@@ -483,6 +483,9 @@ void orc_pool_gradients_brute(int n_so, const double* h, const double* g, const 
 
 // dE/dtheta of the truncated circuit, each truncation a fixed projector P_g
 // onto the kept set S_g:  psi_g = P_g U_g psi_{g-1},  phi_g = U_g psi_{g-1}.
+// S_g holds every determinant of phi_g that the criteria keep, exact zeros
+// included (ranked below every nonzero |c|): with no cut the projector is the
+// identity on phi_g's support and the derivative is exact, also at theta = 0.
 //   nu_M = P_M (H - E) psi_M,  nu_{g-1} = P_{g-1} U_g^dag nu_g,
 //   dE/dtheta_g = 2 <nu_g | A_g phi_g> / <psi_M|psi_M>.
 void orc_energy_grad_eps(int n_so, int n_e, const double* h, const double* g, const uint8_t* ops,
@@ -494,7 +497,10 @@ void orc_energy_grad_eps(int n_so, int n_e, const double* h, const double* g, co
   psi[0][hf] = 1.0;
   for (int k = 0; k < n_ops; ++k) {
     Op o = op_from_bytes(ops + 5 * k);
-    psi[k + 1] = truncate(gate_apply(psi[k], o, std::cos(theta[k]), std::sin(theta[k])), n_keep, eps);
+    // the projectors keep every determinant the gate reaches, zero amplitude
+    // or not, unless a criterion cuts it (a partner at theta = 0 has c = 0
+    // but a nonzero derivative); zeros rank below every nonzero |c|
+    psi[k + 1] = truncate(gate_apply(psi[k], o, std::cos(theta[k]), std::sin(theta[k]), true), n_keep, eps);
   }
   double n2 = 0.0;
   const double e = energy_of(H, psi[n_ops], &n2);
@@ -506,7 +512,7 @@ void orc_energy_grad_eps(int n_so, int n_e, const double* h, const double* g, co
     Op o = op_from_bytes(ops + 5 * k);
     const double c = std::cos(theta[k]), sn = std::sin(theta[k]);
     // A phi, phi = U psi_{k}
-    State phi = gate_apply(psi[k], o, c, sn);
+    State phi = gate_apply(psi[k], o, c, sn, true);
     State aphi;
     for (const auto& kv : phi) {
       Term up = apply_tau(o, kv.first);
@@ -521,7 +527,7 @@ void orc_energy_grad_eps(int n_so, int n_e, const double* h, const double* g, co
     }
     dtheta_out[k] = 2.0 * dot / n2;
     // nu <- P_{k} U^dag nu,  U^dag = U(-theta)
-    State back = gate_apply(nu, o, c, -sn);
+    State back = gate_apply(nu, o, c, -sn, true);
     State proj;
     for (const auto& kv : psi[k]) {
       auto it = back.find(kv.first);

@@ -260,14 +260,19 @@ def test_pool_gradient_at_hf_closed_form(c1):
 
 
 # ---------------------------------------------------------------- adjoint
-def test_adjoint_untruncated_matches_dense_derivative(c1):
+@pytest.mark.parametrize("zeros", [(), (3, 9), tuple(range(10))])
+def test_adjoint_untruncated_matches_dense_derivative(c1, zeros):
+    """Also at theta_g = 0 (a new ADAPT parameter), where the gate's partner
+    determinants have exactly zero amplitude but a nonzero derivative."""
     w, basis, H = c1
-    e, d = O.energy_grad(w.n_so, w.n_e, w.h, w.g, w.ops, w.theta, 0)
+    theta = w.theta.copy()
+    theta[list(zeros)] = 0.0
+    e, d = O.energy_grad(w.n_so, w.n_e, w.h, w.g, w.ops, theta, 0)
     aops = J.annihilators(w.n_so)
     K = [J.kappa_matrix(aops, op) for op in w.ops]
     psis = [np.zeros(1 << w.n_so)]
     psis[0][(1 << w.n_e) - 1] = 1.0
-    for kk, th in zip(K, w.theta):
+    for kk, th in zip(K, theta):
         psis.append(spla.expm_multiply(th * kk, psis[-1]))
     Hfull = np.zeros((1 << w.n_so, 1 << w.n_so))
     Hfull[np.ix_(basis, basis)] = H
@@ -277,7 +282,7 @@ def test_adjoint_untruncated_matches_dense_derivative(c1):
         # d psi_M / d theta_g = U_M..U_{g+1} kappa_g psi_g
         dpsi = K[g] @ psis[g + 1]
         for j in range(g + 1, len(w.ops)):
-            dpsi = spla.expm_multiply(w.theta[j] * K[j], dpsi)
+            dpsi = spla.expm_multiply(theta[j] * K[j], dpsi)
         assert abs(2 * lam @ dpsi - d[g]) < 1e-12
 
 
