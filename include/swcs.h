@@ -127,7 +127,12 @@ int swcs_pool_gradients_dev(swcs_ctx* ctx, double* d_g_out, const int64_t* d_sub
 int swcs_sweep_energy(swcs_ctx* ctx, double* h_e_out, double* h_norm2_out);
 
 /* Energy and dE/dtheta of the truncated ansatz, each truncation held as a
- * fixed projector onto its kept set (Sec. II.B, "analytic gradients").
+ * fixed projector onto its kept set (Sec. II.B, "analytic gradients").  A
+ * kept set holds every determinant the gate reaches, exact-zero amplitudes
+ * included (they rank below every nonzero |c| for the size criterion; the
+ * magnitude criterion drops them): without a cut the projector is the
+ * identity on the reachable determinants, so the derivative is exact, also
+ * at theta_g = 0 where the gate's partner determinants have c = 0.
  * The forward pass keeps a copy of the state every ckpt_every gates
  * (ckpt_every <= 0: 20); the backward pass replays each segment from its
  * checkpoint.  Leaves the final state in the context. */

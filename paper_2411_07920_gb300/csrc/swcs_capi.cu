@@ -345,9 +345,13 @@ int64_t max_state_for(swcs_ctx* c, int64_t n_keep, int n_ops, int64_t n_now) {
   return (int64_t)bound;
 }
 
+// keep_zeros: determinants a gate reaches with an exactly zero amplitude stay
+// in the kept set (ranked below every nonzero |c|) unless a criterion cuts
+// them -- the projectors of the adjoint need them (a partner at theta = 0 has
+// c = 0 but a nonzero derivative); the magnitude criterion still drops them.
 int run_gates(swcs_ctx* c, const uint8_t* d_ops, const double* d_cs, int n_ops, int64_t n_keep, bool reset,
               uint64_t* snap_keys = nullptr, double* snap_amps = nullptr, long long* snap_n = nullptr,
-              int64_t snap_stride = 0) {
+              int64_t snap_stride = 0, bool keep_zeros = false) {
   const int bps = ansatz_blocks_per_sm();
   if (bps <= 0) return fail(c, SWCS_ERR_NO_DEVICE, "ansatz kernel cannot be resident on this device");
   AnsatzArgs a{};
@@ -367,7 +371,7 @@ int run_gates(swcs_ctx* c, const uint8_t* d_ops, const double* d_cs, int n_ops, 
   {  // |c| >= eps <=> abs bit pattern >= eps's bit pattern (IEEE-754 order of non-negative doubles)
     uint64_t eb = 0;
     std::memcpy(&eb, &c->trunc_eps, 8);
-    a.min_abs_bits = (c->trunc_eps > 0.0) ? eb : 1ull;
+    a.min_abs_bits = (c->trunc_eps > 0.0) ? eb : (keep_zeros ? 0ull : 1ull);
   }
   a.reset_to_hf = reset ? 1 : 0;
   a.hf = (c->ne >= 64) ? ~0ull : ((1ull << c->ne) - 1ull);
@@ -1282,7 +1286,8 @@ int swcs_energy_grad(swcs_ctx* c, const uint8_t* h_ops, const double* h_theta, i
   for (int seg = 0; seg < ncp; ++seg) {
     const int g0 = seg * ck, g1 = std::min(n_ops, g0 + ck);
     if (seg > 0 && (r = save_slot(seg))) return r;
-    if ((r = run_gates(c, dops + 5 * g0, dcs + 2 * g0, g1 - g0, n_keep, seg == 0))) return r;
+    if ((r = run_gates(c, dops + 5 * g0, dcs + 2 * g0, g1 - g0, n_keep, seg == 0, nullptr, nullptr, nullptr, 0, true)))
+      return r;
   }
   if ((r = save_slot(ncp))) return r;
   c->have_state = true;
@@ -1310,7 +1315,7 @@ int swcs_energy_grad(swcs_ctx* c, const uint8_t* h_ops, const double* h_theta, i
     if ((r = load_slot(seg))) return r;
     if (g1 - g0 > 1) {
       if ((r = run_gates(c, dops + 5 * g0, dcs + 2 * g0, g1 - g0 - 1, n_keep, false, (uint64_t*)c->sn_keys.p,
-                         (double*)c->sn_amps.p, (long long*)c->sn_n.p, stride)))
+                         (double*)c->sn_amps.p, (long long*)c->sn_n.p, stride, true)))
         return r;
     }
     for (int g = g1 - 1; g >= g0; --g) {
@@ -1346,7 +1351,8 @@ int swcs_energy_grad(swcs_ctx* c, const uint8_t* h_ops, const double* h_theta, i
   }
   CK(launch_k(c, kKOther, [&] { return launch_scale_dtheta((double*)c->dth.p, n_ops, k->acc, c->st); }));
   CK(launch_k(c, kKOther, [&] { return launch_finalize_energy(k->acc, k->eout, c->st); }));
-  // leave psi_M as the context's state (index table rebuilt by an identity pass)
+  // leave psi_M as the context's state (an identity pass rebuilds the index
+  // table and drops the zero amplitudes the projectors kept)
   if ((r = load_slot(ncp))) return r;
   {
     const uint8_t id[5] = {0, 0, 0, 0, 0};

@@ -26,7 +26,7 @@ struct AnsatzArgs {
   const double* cs;    // (cos theta, sin theta) per gate
   int n_ops;
   int64_t n_keep;      // <= 0: no size criterion
-  uint64_t min_abs_bits;  // magnitude criterion: |c| bit patterns below this are dropped (1: exact zeros only)
+  uint64_t min_abs_bits;  // |c| bit patterns below this are dropped (1: exact zeros; 0: none; else the magnitude criterion)
   int reset_to_hf;
   uint64_t hf;
   long long* n_state;  // in: input size (unless reset_to_hf); out: output size

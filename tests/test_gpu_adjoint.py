@@ -78,3 +78,25 @@ def test_autograd_function(S):
     eo, do = O.energy_grad(w.n_so, w.n_e, w.h, w.g, w.ops, w.theta, 80)
     assert abs(e.item() - eo) < TOL
     assert np.abs(g.numpy() - 3.0 * do).max() < 3 * TOL
+
+
+@pytest.mark.parametrize("n_so,n_e,n_ops,seed,n_keep,ckpt,zeros", [
+    (12, 4, 10, 1, 0, 20, (3, 9)), (12, 4, 10, 1, 0, 4, tuple(range(10))), (16, 6, 30, 71, 60, 4, (0, 13, 29)),
+    (20, 6, 45, 72, 300, 20, (44,)), (24, 8, 33, 73, 0, 7, (32,))])
+def test_adjoint_at_zero_angles_matches_oracle(S, n_so, n_e, n_ops, seed, n_keep, ckpt, zeros):
+    """theta_g = 0 (how ADAPT starts a new parameter): the kept sets of the
+    projectors include the gate's zero-amplitude partners."""
+    w = I.small_case(n_so, n_e, n_ops, seed, n_keep=n_keep)
+    theta = w.theta.copy()
+    theta[list(zeros)] = 0.0
+    c = S.Context()
+    c.load_hamiltonian(w.h, w.g, w.n_so, w.n_e)
+    e, d = c.energy_grad(w.ops, theta, n_keep, ckpt)
+    eo, do = O.energy_grad(w.n_so, w.n_e, w.h, w.g, w.ops, theta, n_keep)
+    assert abs(e - eo) < TOL
+    assert np.abs(d - do).max() < TOL, np.abs(d - do).max()
+    if n_keep == 0:
+        assert all(abs(do[z]) > 1e-8 for z in zeros)  # zero angles, nonzero derivatives
+    k, a = c.get_state()
+    ko, ao = O.apply_ansatz(w.n_so, w.n_e, w.ops, theta, n_keep)
+    assert np.array_equal(k, ko) and np.array_equal(a, ao)
