@@ -16,6 +16,11 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
   pool_gradients        brute-force definition (A_k psi formed explicitly),
                         finite differences of the energy, HF closed form,
                         pool size closed form
-  energy_grad           central finite differences of the truncated energy
+  energy_grad           central finite differences of the truncated energy,
+                        dense derivative of the untruncated circuit (zero angles too)
+  adapt (ADAPT-VQE loop, BFGS-2 / BFGS-2F bootstrap), in tests/test_adapt_oracle.py:
+                        two-level ground state of the first iteration, exact
+                        one-parameter minimum of BFGS-2's first step, variational
+                        bound and monotone energies against dense FCI
 """
 from .oracle import *  # noqa: F401,F403

@@ -7,8 +7,10 @@ The loop, step by step as Fig. 1 orders it, on top of the oracle's SWCS:
           appended to the end of the current (truncated) ansatz;
   step 5  converged when ||g|| < eps;
   step 6  append the operator with the largest |g_k|, its parameter 0
-          (reading: values within a relative 1e-9 of the largest count as
-          equal, and the first of them in canonical pool order is taken);
+          (reading: values within a relative 1e-5 of the largest count as
+          equal -- spin-partner operators of a spin-symmetric state differ
+          only by the optimiser's tolerance -- and the first of them in
+          canonical pool order is taken);
   step 7  VQE: BFGS over all parameters, energy and gradient of the
           truncated circuit from the oracle's adjoint.
 BFGS-2 replaces step 7 by (1) BFGS over the new parameter alone, the others
@@ -34,7 +36,7 @@ import scipy.optimize as so
 from . import oracle as O
 
 
-def _largest(g, rel=1e-9):
+def _largest(g, rel=1e-5):
     mag = np.abs(np.asarray(g, np.float64))
     top = mag.max()
     for k in range(len(mag)):
@@ -57,6 +59,7 @@ class OracleAdapt:
         self.energies = []
         self.grad_norms = []
         self.calls = 0
+        self.stalled = False
 
     def _eg(self, theta):
         self.calls += 1
@@ -79,30 +82,45 @@ class OracleAdapt:
         r = so.minimize(f, theta[-1:], jac=True, method="BFGS", options={"gtol": self.gtol})
         return np.concatenate([head, np.asarray(r.x, np.float64)])
 
+    def _energy(self, ops, theta):
+        keys, amps = O.apply_ansatz(self.n_so, self.n_e, ops, theta, self.n_keep)
+        return O.energy(self.n_so, self.h, self.g, keys, amps)[0]
+
     def iterate(self, mode="bfgs"):
-        """One pass of steps 4-7; returns False once converged (step 5)."""
+        """One pass of steps 4-7; returns False once converged (step 5) or
+        stalled (reading: an optimisation that lowers E by less than 1e-12 is
+        undone and ends the run, since the same operator would be chosen
+        again)."""
         g = self.pool_gradient()
         norm = float(np.sqrt(np.sum(g * g)))
         self.grad_norms.append(norm)
+        self.stalled = False
         if norm < self.eps:
             return False
+        e_before = self._energy(self.ops, self.theta)
         k = _largest(g)
-        self.chosen.append(k)
-        self.ops = np.concatenate([self.ops, self.pool[k][None, :]])
+        ops = np.concatenate([self.ops, self.pool[k][None, :]])
+        old_ops, self.ops = self.ops, ops
         theta = np.concatenate([self.theta, [0.0]])
         if mode in ("bfgs2", "bfgs2f"):
             theta = self._bfgs_last(theta)
         if mode in ("bfgs", "bfgs2"):
             theta = self._bfgs_all(theta)
+        e_after = self._energy(ops, theta)
+        if not e_after < e_before - 1e-12:
+            self.ops = old_ops
+            self.stalled = True
+            return False
+        self.chosen.append(k)
         self.theta = theta
-        keys, amps = O.apply_ansatz(self.n_so, self.n_e, self.ops, theta, self.n_keep)
-        self.energies.append(O.energy(self.n_so, self.h, self.g, keys, amps)[0])
+        self.energies.append(e_after)
         return True
 
     def run(self, max_iter, mode="bfgs"):
+        """True when converged (||g|| < eps); False when stalled or out of iterations."""
         for _ in range(max_iter):
             if not self.iterate(mode):
-                return True
+                return not self.stalled
         return False
 
 
@@ -114,5 +132,5 @@ def bootstrap(n_so, n_e, h, g, schedule, max_iter, eps=1e-2, gtol=1e-6, first="b
     for i, n_keep in enumerate(schedule):
         a.n_keep = n_keep
         conv = a.run(max_iter, first if i == 0 else then)
-        stages.append(dict(n_keep=n_keep, n_params=len(a.theta), converged=conv))
+        stages.append(dict(n_keep=n_keep, n_params=len(a.theta), converged=conv, stalled=a.stalled))
     return a, stages
