@@ -56,6 +56,9 @@ def parse():
     p.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched leg")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     p.add_argument("--no-screen", action="store_true", help="skip the learned-screening leg")
+    p.add_argument("--no-adapt", action="store_true", help="skip the ADAPT-VQE leg")
+    p.add_argument("--adapt-n-keep", type=int, default=10_000, help="N_CUT of the ADAPT-VQE leg")
+    p.add_argument("--adapt-iters", type=int, default=30, help="ADAPT iterations of the ADAPT-VQE leg")
     return p.parse_args()
 
 
@@ -327,6 +330,11 @@ def run_swcs(args):
     if not args.no_batch:
         batch = run_batch_leg(swcs, I, torch)
 
+    # ------------------------------------------------------------ ADAPT-VQE leg (same Hamiltonian, from HF)
+    adapt_res = None
+    if not args.no_adapt:
+        adapt_res = run_adapt_leg(swcs, w, args, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle as O
@@ -345,7 +353,7 @@ def run_swcs(args):
                            "parallelism": f"replicas x{world}", "l2": "flushed between steps (512 MB write)"},
                 "gate_dets_per_s": gate_dets_per_s, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "energy_ms": round(min(energy_ms), 3),
-                "adjoint": adjoint, "batch": batch, "screen": screen_res,
+                "adjoint": adjoint, "batch": batch, "screen": screen_res, "adapt": adapt_res,
                 "kernels_ms": {k: round(v[0], 3) for k, v in prof.items()},
                 "ext": {"distinct": stats["ext_distinct"], "buckets": stats["ext_buckets"],
                         "capacity": stats["ext_capacity"]}}
@@ -433,6 +441,33 @@ def run_screen_leg(swcs, ctx, w, args, torch, frac=0.05):
             "train_s": round(t_train, 2), "train_samples": int(X.shape[0]), "train_loss": hist[-1][1],
             "mlp_forward": {"ms": round(1e3 * t_fwd, 4), "tflops": round(flops / t_fwd / 1e12, 2),
                             "frac_of_bf16_peak": round(flops / t_fwd / 1e12 / bf16_peak, 4)}}
+
+
+def run_adapt_leg(swcs, w, args, torch):
+    """ADAPT-VQE with BFGS-2 on the benchmark Hamiltonian from the reference
+    determinant at N_CUT = args.adapt_n_keep: wall time per iteration, split
+    into the pool sweep (step 4) and the VQE over swcs_energy_grad (step 7)."""
+    from paper_2411_07920_gb300 import adapt
+    c = swcs.Context()
+    c.load_hamiltonian(w.h, w.g, w.n_so, w.n_e)
+    a = adapt.Adapt(c, args.adapt_n_keep, eps=1e-3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    a.run(args.adapt_iters, "bfgs2")
+    total = time.perf_counter() - t0
+    its = [it for it in a.history if it.op_index >= 0 and not it.stalled]
+    t_pool = sum(it.t_pool_s for it in a.history)
+    t_vqe = sum(it.t_vqe_s for it in a.history)
+    res = {"workload": f"{w.n_so} spin-orbitals, {w.n_e} electrons, GSD pool, N_CUT={args.adapt_n_keep}, BFGS-2 "
+                       "from the reference determinant",
+           "iterations": len(its), "ms_per_iteration": round(1e3 * total / max(1, len(a.history)), 3),
+           "pool_ms": round(1e3 * t_pool, 3), "vqe_ms": round(1e3 * t_vqe, 3),
+           "vqe_share": round(t_vqe / total, 4) if total > 0 else None,
+           "energy_grad_calls": int(sum(it.energy_grad_calls for it in a.history)),
+           "dets": [int(it.n_dets) for it in its], "energies": [float(it.energy) for it in its],
+           "grad_norms": [float(it.grad_norm) for it in a.history]}
+    c.close()
+    return res
 
 
 def run_batch_leg(swcs, I, torch, n_inst=64, seed0=100, reps=3):

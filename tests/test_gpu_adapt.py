@@ -1,0 +1,57 @@
+"""ADAPT-VQE through the library (paper_2411_07920_gb300.adapt) against the
+oracle's loop: the same operators chosen in the same order, energies within
+1e-8, parameters within 1e-5, the same stopping decisions."""
+import numpy as np
+import pytest
+
+from oracle.adapt import OracleAdapt, bootstrap as oracle_bootstrap
+from paper_2411_07920_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def A():
+    from paper_2411_07920_gb300 import adapt, swcs
+    return adapt, swcs
+
+
+def _ctx(swcs, w):
+    c = swcs.Context()
+    c.load_hamiltonian(w.h, w.g, w.n_so, w.n_e)
+    return c
+
+
+def _accepted(a):
+    return [it.energy for it in a.history if it.op_index >= 0 and not it.stalled]
+
+
+@pytest.mark.parametrize("n_so,n_e,seed,n_keep,mode,iters", [
+    (12, 4, 1, 0, "bfgs", 12), (16, 6, 2, 150, "bfgs2", 8), (16, 6, 3, 0, "bfgs2f", 8), (20, 6, 4, 40, "bfgs", 30)])
+def test_adapt_matches_oracle(A, n_so, n_e, seed, n_keep, mode, iters):
+    adapt, swcs = A
+    w = I.small_case(n_so, n_e, 1, seed)
+    ref = OracleAdapt(w.n_so, w.n_e, w.h, w.g, n_keep, eps=1e-3)
+    conv_ref = ref.run(iters, mode)
+    a = adapt.Adapt(_ctx(swcs, w), n_keep, eps=1e-3)
+    conv = a.run(iters, mode)
+    assert conv == conv_ref
+    assert a.chosen == ref.chosen
+    assert bool(a.history[-1].stalled) == bool(ref.stalled)
+    assert np.abs(np.array(_accepted(a)) - np.array(ref.energies)).max() < 1e-8
+    assert np.abs(a.theta - ref.theta).max() < 1e-5
+    assert abs(a.history[0].grad_norm - ref.grad_norms[0]) < 1e-10
+    assert all(it.energy_grad_calls > 0 for it in a.history if it.op_index >= 0)
+
+
+def test_bootstrap_matches_oracle(A):
+    adapt, swcs = A
+    w = I.small_case(20, 6, 1, 5)
+    sched = [30, 90, 270]
+    ref, st_ref = oracle_bootstrap(w.n_so, w.n_e, w.h, w.g, sched, 6, eps=1e-3)
+    a, st = adapt.bootstrap(_ctx(swcs, w), sched, 6, eps=1e-3)
+    assert [s["n_params"] for s in st] == [s["n_params"] for s in st_ref]
+    assert [s["converged"] for s in st] == [s["converged"] for s in st_ref]
+    assert [s["stalled"] for s in st] == [s["stalled"] for s in st_ref]
+    assert a.chosen == ref.chosen
+    assert np.abs(np.array(_accepted(a)) - np.array(ref.energies)).max() < 1e-8
