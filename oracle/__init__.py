@@ -22,5 +22,8 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
                         two-level ground state of the first iteration, exact
                         one-parameter minimum of BFGS-2's first step, variational
                         bound and monotone energies against dense FCI
+  spin (spin-complemented pool), in tests/test_spin_oracle.py: paired gradients
+                        on flip-symmetrised states, commuting pairs against the
+                        exponential of the summed generator
 """
 from .oracle import *  # noqa: F401,F403

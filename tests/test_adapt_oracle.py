@@ -75,8 +75,7 @@ def test_bfgs2_first_step_is_the_exact_one_parameter_minimum(c1):
     g = a.pool_gradient()
     k = int(np.argmax(np.abs(g)))
     ops = np.concatenate([a.ops, a.pool[k][None, :]])
-    a.ops = ops
-    theta = a._bfgs_last(np.append(a.theta, 0.0))
+    theta = a._bfgs_last(np.append(a.theta, 0.0), a.chosen + [k])
     t_star = theta[-1]
 
     def e_of(t):
