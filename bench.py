@@ -444,13 +444,14 @@ def run_screen_leg(swcs, ctx, w, args, torch, frac=0.05):
 
 
 def run_adapt_leg(swcs, w, args, torch):
-    """ADAPT-VQE with BFGS-2 on the benchmark Hamiltonian from the reference
-    determinant at N_CUT = args.adapt_n_keep: wall time per iteration, split
+    """ADAPT-VQE with BFGS-2 over the spin-complemented pool on the benchmark
+    Hamiltonian from the reference determinant at N_CUT = args.adapt_n_keep:
+    wall time per iteration, split
     into the pool sweep (step 4) and the VQE over swcs_energy_grad (step 7)."""
     from paper_2411_07920_gb300 import adapt
     c = swcs.Context()
     c.load_hamiltonian(w.h, w.g, w.n_so, w.n_e)
-    a = adapt.Adapt(c, args.adapt_n_keep, eps=1e-3)
+    a = adapt.Adapt(c, args.adapt_n_keep, eps=1e-3, pool_kind="spin")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     a.run(args.adapt_iters, "bfgs2")
@@ -458,8 +459,8 @@ def run_adapt_leg(swcs, w, args, torch):
     its = [it for it in a.history if it.op_index >= 0 and not it.stalled]
     t_pool = sum(it.t_pool_s for it in a.history)
     t_vqe = sum(it.t_vqe_s for it in a.history)
-    res = {"workload": f"{w.n_so} spin-orbitals, {w.n_e} electrons, GSD pool, N_CUT={args.adapt_n_keep}, BFGS-2 "
-                       "from the reference determinant",
+    res = {"workload": f"{w.n_so} spin-orbitals, {w.n_e} electrons, spin-complemented GSD pool, "
+                       f"N_CUT={args.adapt_n_keep}, BFGS-2 from the reference determinant",
            "iterations": len(its), "ms_per_iteration": round(1e3 * total / max(1, len(a.history)), 3),
            "pool_ms": round(1e3 * t_pool, 3), "vqe_ms": round(1e3 * t_vqe, 3),
            "vqe_share": round(t_vqe / total, 4) if total > 0 else None,

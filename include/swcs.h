@@ -88,6 +88,16 @@ int swcs_load_hamiltonian(swcs_ctx* ctx, const double* h_h, const double* h_g, i
 int swcs_pool_size(swcs_ctx* ctx, int64_t* n_out);
 int swcs_pool_ops(swcs_ctx* ctx, uint8_t* h_ops_out /* 5*pool_size bytes */);
 
+/* Spin complements of the pool operators (Sec. III: spin-complemented
+ * operators for closed-shell molecules).  With F the spin flip of every
+ * spin-orbital (2i + s -> 2i + 1 - s), the flipped generator F(kappa_k) equals
+ * sign[k] * kappa_{partner[k]}, kappa = tau - tau^dag.  The spin-complemented
+ * operator of the pair is kappa_k + sign[k] kappa_{partner[k]} (2 kappa_k when
+ * partner[k] == k and sign[k] == +1; zero, hence not an operator, when
+ * partner[k] == k and sign[k] == -1); its gradient is g_k + sign[k] g_partner.
+ *   partner  [pool_size] host, int64;  sign  [pool_size] host, +1 or -1. */
+int swcs_pool_spin_pairs(swcs_ctx* ctx, int64_t* partner, int8_t* sign);
+
 /* Evaluate the ansatz (Eq. 1) from |Psi_0>, truncating to n_keep after every
  * gate (n_keep <= 0: no truncation).  h_ops: 5*n_ops bytes; h_theta: n_ops.
  * The resulting state stays on the device in the context. */

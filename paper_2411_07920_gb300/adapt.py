@@ -13,6 +13,14 @@ largest |g_k| with parameter 0 and re-optimise:
   "bfgs"    BFGS over all parameters;
   "bfgs2"   BFGS over the new parameter alone (the others frozen), then over all;
   "bfgs2f"  the first half only (the others stay frozen).
+With pool="spin" the candidates are the spin-complemented operators of
+Sec. III: kappa_k + s kappa_j for each pair the library's
+swcs_pool_spin_pairs reports (flip(kappa_k) = s kappa_j), one parameter t
+applied as the two gates exp(t kappa_k) exp(s t kappa_j) -- a
+self-complementary operator as the one gate exp(2 t kappa_k) -- so its pool
+gradient is g_k + s g_j and its parameter gradient the chain-rule sum over
+its gates.
+
 Conventions where the paper is silent: |g_k| within a relative 1e-5 of the
 largest count as equal (spin-partner operators of a spin-symmetric state
 differ only by the optimiser's tolerance) and the first in canonical pool
@@ -61,33 +69,79 @@ class Adapt:
     gtol: float = 1e-6
     ckpt_every: int = 20
     stall: float = 1e-12
-    ops: np.ndarray = field(default_factory=lambda: np.zeros((0, 5), np.uint8))
-    theta: np.ndarray = field(default_factory=lambda: np.zeros(0))
-    chosen: list = field(default_factory=list)
+    pool_kind: str = "gsd"      # "gsd": every pool operator; "spin": spin-complemented pairs
+    theta: np.ndarray = field(default_factory=lambda: np.zeros(0))  # one per chosen candidate
+    chosen: list = field(default_factory=list)                      # candidate indices, in order
     history: list = field(default_factory=list)
 
     def __post_init__(self):
         self.pool = self.ctx.pool_ops()
+        P = len(self.pool)
+        if self.pool_kind == "spin":
+            partner, sign = self.ctx.pool_spin_pairs()
+            k = np.arange(P)
+            keep = (k < partner) | ((k == partner) & (sign == 1))
+            self.unit_k = k[keep]
+            self.unit_j = partner[keep]
+            self.unit_s = sign[keep].astype(np.float64)
+        elif self.pool_kind == "gsd":
+            self.unit_k = np.arange(P)
+            self.unit_j = np.full(P, -1, np.int64)
+            self.unit_s = np.ones(P)
+        else:
+            raise ValueError(f"unknown pool {self.pool_kind!r}")
         self._calls = 0
 
-    def _energy_grad(self, ops, theta):
+    def _expand(self, chosen, theta):
+        """Gates of the chosen units: (ops, gate angles, owner unit, factor)."""
+        owner, factor, idx = [], [], []
+        for i, u in enumerate(chosen):
+            k, j, s = int(self.unit_k[u]), int(self.unit_j[u]), float(self.unit_s[u])
+            if j < 0:
+                idx.append(k); owner.append(i); factor.append(1.0)
+            elif j == k:
+                idx.append(k); owner.append(i); factor.append(2.0)
+            else:
+                idx += [k, j]; owner += [i, i]; factor += [1.0, s]
+        owner = np.asarray(owner, np.int64)
+        factor = np.asarray(factor)
+        ops = self.pool[np.asarray(idx, np.int64)] if idx else np.zeros((0, 5), np.uint8)
+        return ops, np.asarray(theta)[owner] * factor, owner, factor
+
+    @property
+    def ops(self):
+        """Gate list of the current ansatz."""
+        return self._expand(self.chosen, self.theta)[0]
+
+    def _energy_grad(self, chosen, theta):
         self._calls += 1
-        return self.ctx.energy_grad(ops, theta, self.n_keep, self.ckpt_every)
+        ops, ang, owner, factor = self._expand(chosen, theta)
+        e, d = self.ctx.energy_grad(ops, ang, self.n_keep, self.ckpt_every)
+        return e, np.bincount(owner, weights=d * factor, minlength=len(theta))
+
+    def _apply(self, chosen, theta):
+        ops, ang, _, _ = self._expand(chosen, theta)
+        self.ctx.apply_ansatz(ops, ang, self.n_keep)
 
     def energy(self):
-        self.ctx.apply_ansatz(self.ops, self.theta, self.n_keep)
+        self._apply(self.chosen, self.theta)
         return self.ctx.energy()[0]
 
     def pool_gradient(self):
-        self.ctx.apply_ansatz(self.ops, self.theta, self.n_keep)
-        return self.ctx.pool_gradients()
+        """Step 4: the gradient of every candidate appended at the end."""
+        self._apply(self.chosen, self.theta)
+        g = self.ctx.pool_gradients()
+        out = g[self.unit_k].copy()
+        pair = self.unit_j >= 0
+        out[pair] += self.unit_s[pair] * g[self.unit_j[pair]]
+        return out
 
-    def _minimize(self, ops, theta, free):
+    def _minimize(self, chosen, theta, free):
         """BFGS over theta[free:] with theta[:free] frozen."""
         frozen = theta[:free].copy()
 
         def fun(x):
-            e, d = self._energy_grad(ops, np.concatenate([frozen, x]))
+            e, d = self._energy_grad(chosen, np.concatenate([frozen, x]))
             return e, d[free:]
         res = opt.minimize(fun, theta[free:], jac=True, method="BFGS", options={"gtol": self.gtol})
         return np.concatenate([frozen, np.asarray(res.x, np.float64)])
@@ -105,16 +159,16 @@ class Adapt:
             self.history.append(it)
             return False
         k = largest_gradient(g)
-        ops = np.concatenate([self.ops, self.pool[k:k + 1]])
+        chosen = self.chosen + [k]
         theta = np.append(self.theta, 0.0)
         calls0 = self._calls
         if optimizer in ("bfgs2", "bfgs2f"):
-            theta = self._minimize(ops, theta, len(theta) - 1)
+            theta = self._minimize(chosen, theta, len(theta) - 1)
         if optimizer in ("bfgs", "bfgs2"):
-            theta = self._minimize(ops, theta, 0)
+            theta = self._minimize(chosen, theta, 0)
         if optimizer not in ("bfgs", "bfgs2", "bfgs2f"):
             raise ValueError(f"unknown optimizer {optimizer!r}")
-        self.ctx.apply_ansatz(ops, theta, self.n_keep)
+        self._apply(chosen, theta)
         e_after = self.ctx.energy()[0]
         it.t_vqe_s = time.perf_counter() - t1
         it.energy_grad_calls = self._calls - calls0
@@ -124,8 +178,7 @@ class Adapt:
             it.energy = e_before
             self.history.append(it)
             return False
-        self.ops, self.theta = ops, theta
-        self.chosen.append(k)
+        self.chosen, self.theta = chosen, theta
         it.energy = e_after
         it.n_params = len(theta)
         it.n_dets = self.ctx.state_size()

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -861,6 +862,47 @@ int swcs_pool_ops(swcs_ctx* c, uint8_t* out) {
   if (r) return r;
   if (!out) return fail(c, SWCS_ERR_INVALID_ARG, "null output");
   memcpy(out, c->pool_ops.data(), c->pool_ops.size());
+  return SWCS_OK;
+}
+
+// Spin complement of every pool operator (Sec. III uses spin-complemented
+// operators for the closed-shell molecules): spin-orbital p = 2i + s maps to
+// 2i + (1 - s).  The flipped generator equals sign[k] times the generator of
+// pool operator partner[k]; it is found as the flipped string brought to the
+// pool's index order, or as the adjoint of a pool operator (then the
+// generator changes sign).
+int swcs_pool_spin_pairs(swcs_ctx* c, int64_t* partner, int8_t* sign) {
+  int r = need_ham(c);
+  if (r) return r;
+  if (!partner || !sign) return fail(c, SWCS_ERR_INVALID_ARG, "null output");
+  auto pack = [](int kind, int a, int b, int x, int y) {
+    return ((uint64_t)kind << 32) | ((uint64_t)a << 24) | ((uint64_t)b << 16) | ((uint64_t)x << 8) | (uint64_t)y;
+  };
+  std::unordered_map<uint64_t, int64_t> at;
+  at.reserve((size_t)c->pool_size * 2);
+  for (int64_t k = 0; k < c->pool_size; ++k) {
+    const uint8_t* o = &c->pool_ops[(size_t)5 * k];
+    at.emplace(pack(o[0], o[1], o[2], o[3], o[4]), k);
+  }
+  for (int64_t k = 0; k < c->pool_size; ++k) {
+    const uint8_t* o = &c->pool_ops[(size_t)5 * k];
+    int p = o[1] ^ 1, q = o[2] ^ 1, x = o[3] ^ 1, y = o[4] ^ 1, sg = 1;
+    auto it = at.end();
+    if (o[0] == 1) {
+      it = at.find(pack(1, p, q, 0, 0));  // same spin: the flip keeps p < q
+    } else {
+      if (p > q) { std::swap(p, q); sg = -sg; }  // a_q a_p with p < q
+      if (x > y) { std::swap(x, y); sg = -sg; }  // a+_x a+_y with x < y
+      it = at.find(pack(2, p, q, x, y));
+      if (it == at.end()) {
+        it = at.find(pack(2, x, y, p, q));  // adjoint of a pool operator
+        sg = -sg;
+      }
+    }
+    if (it == at.end()) return fail(c, SWCS_ERR_INVALID_ARG, "pool operator %lld has no spin complement", (long long)k);
+    partner[k] = it->second;
+    sign[k] = (int8_t)sg;
+  }
   return SWCS_OK;
 }
 

@@ -40,6 +40,7 @@ _SIGS = {
     "swcs_load_hamiltonian": ([_vp, _vp, _vp, _i, _i], _i),
     "swcs_pool_size": ([_vp, _p64], _i),
     "swcs_pool_ops": ([_vp, _vp], _i),
+    "swcs_pool_spin_pairs": ([_vp, _vp, _vp], _i),
     "swcs_apply_ansatz": ([_vp, _vp, _vp, _i, _i64], _i),
     "swcs_apply_ansatz_dev": ([_vp, _vp, _vp, _i, _i64], _i),
     "swcs_apply_gates": ([_vp, _vp, _vp, _i, _i64], _i),
@@ -319,6 +320,14 @@ class Context:
         out = np.zeros(5 * self.pool_size(), np.uint8)
         self._ck(lib.swcs_pool_ops(self._h, _ptr(out)))
         return out.reshape(-1, 5)
+
+    def pool_spin_pairs(self):
+        """(partner, sign): the spin flip of kappa_k is sign[k] * kappa_partner[k]."""
+        n = self.pool_size()
+        partner = np.zeros(n, np.int64)
+        sign = np.zeros(n, np.int8)
+        self._ck(lib.swcs_pool_spin_pairs(self._h, _ptr(partner), _ptr(sign)))
+        return partner, sign
 
     def apply_ansatz(self, ops, theta, n_keep):
         ops = _c(ops, np.uint8).reshape(-1)

@@ -55,3 +55,31 @@ def test_bootstrap_matches_oracle(A):
     assert [s["stalled"] for s in st] == [s["stalled"] for s in st_ref]
     assert a.chosen == ref.chosen
     assert np.abs(np.array(_accepted(a)) - np.array(ref.energies)).max() < 1e-8
+
+
+@pytest.mark.parametrize("n_so", [12, 28, 52])
+def test_spin_pairs_match_oracle(A, n_so):
+    from oracle.spin import spin_pairs
+    import oracle as O
+    adapt, swcs = A
+    w = I.small_case(n_so, 4 if n_so == 12 else 8, 1, 1)
+    c = _ctx(swcs, w)
+    partner, sign = c.pool_spin_pairs()
+    po, so = spin_pairs(O.pool_ops(n_so))
+    assert np.array_equal(partner, po) and np.array_equal(sign, so)
+
+
+@pytest.mark.parametrize("n_so,n_e,seed,n_keep,mode,iters", [
+    (12, 4, 1, 0, "bfgs", 10), (16, 6, 2, 200, "bfgs2", 6), (20, 6, 4, 60, "bfgs2f", 8)])
+def test_spin_complemented_adapt_matches_oracle(A, n_so, n_e, seed, n_keep, mode, iters):
+    adapt, swcs = A
+    w = I.small_case(n_so, n_e, 1, seed)
+    ref = OracleAdapt(w.n_so, w.n_e, w.h, w.g, n_keep, eps=1e-3, pool="spin")
+    conv_ref = ref.run(iters, mode)
+    a = adapt.Adapt(_ctx(swcs, w), n_keep, eps=1e-3, pool_kind="spin")
+    conv = a.run(iters, mode)
+    assert conv == conv_ref
+    assert a.chosen == ref.chosen
+    assert np.array_equal(a.ops, ref.ops)
+    assert np.abs(np.array(_accepted(a)) - np.array(ref.energies)).max() < 1e-8
+    assert np.abs(a.theta - ref.theta).max() < 1e-5
