@@ -99,7 +99,11 @@ __device__ __forceinline__ int double_phase(uint64_t d, int a0, int a1, int c2, 
   return par;
 }
 
-__device__ __forceinline__ double apply_sign(double v, int sign_bit) { return sign_bit ? -v : v; }
+// -v when sign_bit is set, as a flip of the IEEE-754 sign bit on the integer
+// pipe (the same value as negation, zeros and NaNs included).
+__device__ __forceinline__ double apply_sign(double v, int sign_bit) {
+  return __longlong_as_double(__double_as_longlong(v) ^ ((long long)(sign_bit != 0) << 63));
+}
 
 // ----------------------------------------------------------------------------
 // A gate operator (5 bytes: kind, i0..i3; kind 1: tau = a+_{i1} a_{i0},

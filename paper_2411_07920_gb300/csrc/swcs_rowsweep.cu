@@ -95,8 +95,13 @@ __device__ __forceinline__ double fock_single(const RowArgs& A, const uint8_t* o
   return f;
 }
 
+// Entries receive several contributions: the atomic is issued only while the
+// bit still reads as clear (two lanes that both see it clear both set it).
 __device__ __forceinline__ void mark(unsigned* touched, uint32_t i) {
-  if (touched) atomicOr(&touched[i >> 5], 1u << (i & 31));
+  if (touched) {
+    const unsigned bit = 1u << (i & 31);
+    if (!(touched[i >> 5] & bit)) atomicOr(&touched[i >> 5], bit);
+  }
 }
 
 // One connected pair, scatter or gather.  (p<q) removed, (r<s) added for
