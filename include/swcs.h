@@ -256,6 +256,13 @@ int swcs_mlp_param_count(swcs_mlp* m, int64_t* n_out);
 int swcs_mlp_set_params(swcs_mlp* m, const float* h_params);
 int swcs_mlp_get_params(swcs_mlp* m, float* h_params);
 int swcs_mlp_forward_dev(swcs_mlp* m, const uint16_t* d_x, int64_t n, float* d_y);
+/* Inference: the same y as swcs_mlp_forward_dev (bit for bit) from one fused
+ * kernel that keeps both hidden layers on chip (TMA loads, tcgen05 MMAs into
+ * tensor memory); the activations of swcs_mlp_activations are not written.
+ * Networks whose weights and tiles exceed one SM's shared memory (d_in = 64
+ * with width 256) run layer by layer instead.  d_x: [n x d_in] BF16 bits,
+ * 16-byte aligned; d_y: [n] device. */
+int swcs_mlp_predict_dev(swcs_mlp* m, const uint16_t* d_x, int64_t n, float* d_y);
 int swcs_mlp_grad_dev(swcs_mlp* m, const uint16_t* d_x, const float* d_t, int64_t n, float* d_grad, double* d_loss);
 int swcs_mlp_train_step_dev(swcs_mlp* m, const uint16_t* d_x, const float* d_t, int64_t n, float lr, double* d_loss);
 int swcs_mlp_activations(swcs_mlp* m, uint16_t* h_H1, uint16_t* h_H2, float* h_y, int64_t n);

@@ -1182,7 +1182,7 @@ int swcs_pool_screen_dev(swcs_ctx* c, swcs_mlp* m, double frac, int64_t* d_subse
       (r = ensure(c, c->topk_hist, 2 * 65536 * 4)) || (r = ensure(c, c->topk_ctl, 8 * 8)))
     return r;
   if ((r = swcs_pool_features_dev(c, (uint16_t*)c->feat.p))) return r;
-  if ((r = swcs_mlp_forward_dev(m, (const uint16_t*)c->feat.p, P, (float*)c->ypred.p)))
+  if ((r = swcs_mlp_predict_dev(m, (const uint16_t*)c->feat.p, P, (float*)c->ypred.p)))
     return fail(c, r, "screening network: %s", swcs_mlp_last_error(m));
   CK(launch_k(c, kKOther, [&] {
     return launch_topk((const float*)c->ypred.p, P, k, (unsigned*)c->topk_hist.p, (unsigned long long*)c->topk_ctl.p,

@@ -1,6 +1,7 @@
 // Internal interface between the C-ABI host code and the kernels.
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cuda_bf16.h>
@@ -216,6 +217,20 @@ struct MlpParams {
   __nv_bfloat16* w3b;
 };
 cudaError_t launch_mlp_gemm(const GemmArgs& g, cudaStream_t st);
+// Fused inference forward (all three layers in one persistent tcgen05 kernel).
+struct FusedArgs {
+  int64_t M;                // rows (pool operators)
+  int d_in, width;          // d_in % 16 == 0, 16..64; width % 16 == 0, 16..256
+  const float* b1;          // [width]
+  const float* b2;          // [width]
+  const __nv_bfloat16* w3;  // [width]
+  const float* b3;          // [1]
+  float* y;                 // [M]
+  int* err;
+};
+size_t mlp_fused_smem_bytes(int d_in, int width);
+cudaError_t launch_mlp_fused(const CUtensorMap& tm_x, const CUtensorMap& tm_w1, const CUtensorMap& tm_w2,
+                             const FusedArgs& f, int nblocks, cudaStream_t st);
 cudaError_t launch_mlp_dy(const float* y, const float* t, int B, float* dy, double* loss, cudaStream_t st);
 cudaError_t launch_mlp_dz2(const float* dy, const __nv_bfloat16* w3, const __nv_bfloat16* H2, int B, int W,
                            __nv_bfloat16* dZ2, float* dw3, float* db3, cudaStream_t st);

@@ -3,6 +3,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -103,6 +105,64 @@ int forward(swcs_mlp* m, const __nv_bfloat16* x, int64_t n, float* y) {
   g2.y = y;
   MCK(launch_mlp_gemm(g2, m->st));
   m->launches += 2;
+  return SWCS_OK;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// Row-major BF16 [rows x inner] with boxes of 8 inner elements (16 bytes) x box_rows rows.
+bool k_major_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_t rows, uint32_t box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || ((uintptr_t)base & 15) || (inner * 2) % 16) return false;
+  const cuuint64_t dims[2] = {inner, rows};
+  const cuuint64_t strides[1] = {inner * 2};
+  const cuuint32_t box[2] = {8, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// y = network(x) with the fused kernel; 1 when the shape does not suit it.
+int predict_fused(swcs_mlp* m, const __nv_bfloat16* x, int64_t n, float* y) {
+  const int D = m->p.d_in, W = m->p.width;
+  if (D % 16 || D < 16 || D > 64 || W % 16 || W < 16 || W > 256 || ((uintptr_t)x & 15)) return 1;
+  int dev = 0, nsm = 0, optin = 0;
+  MCK(cudaGetDevice(&dev));
+  MCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  MCK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (mlp_fused_smem_bytes(D, W) > (size_t)optin) return 1;
+  CUtensorMap tx, tw1, tw2;
+  if (!k_major_map(&tx, x, (uint64_t)D, (uint64_t)n, 128) ||
+      !k_major_map(&tw1, m->p.W1b, (uint64_t)D, (uint64_t)W, (uint32_t)W) ||
+      !k_major_map(&tw2, m->p.W2b, (uint64_t)W, (uint64_t)W, (uint32_t)W))
+    return 1;
+  FusedArgs f{};
+  f.M = n;
+  f.d_in = D;
+  f.width = W;
+  f.b1 = m->p.master + m->p.off_b1;
+  f.b2 = m->p.master + m->p.off_b2;
+  f.w3 = m->p.w3b;
+  f.b3 = m->p.master + m->p.off_b3;
+  f.y = y;
+  f.err = m->err_dev;
+  const int64_t tiles = (n + 127) / 128;
+  MCK(launch_mlp_fused(tx, tw1, tw2, f, (int)(tiles < nsm ? tiles : nsm), m->st));
+  m->launches += 1;
   return SWCS_OK;
 }
 
@@ -232,6 +292,13 @@ int swcs_mlp_forward_dev(swcs_mlp* m, const uint16_t* d_x, int64_t n, float* d_y
   if ((r = ensure_rows(m, n))) return r;
   if ((r = forward(m, (const __nv_bfloat16*)d_x, n, d_y))) return r;
   return add_b3(m, d_y, n);
+}
+
+int swcs_mlp_predict_dev(swcs_mlp* m, const uint16_t* d_x, int64_t n, float* d_y) {
+  if (!m || !d_x || !d_y || n <= 0 || n > ((int64_t)1 << 31)) return SWCS_ERR_INVALID_ARG;
+  const int r = predict_fused(m, (const __nv_bfloat16*)d_x, n, d_y);
+  if (r != 1) return r;
+  return swcs_mlp_forward_dev(m, d_x, n, d_y);  // layer by layer, same result
 }
 
 int swcs_mlp_grad_dev(swcs_mlp* m, const uint16_t* d_x, const float* d_t, int64_t n, float* d_grad, double* d_loss) {

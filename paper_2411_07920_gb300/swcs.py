@@ -77,6 +77,7 @@ _SIGS = {
     "swcs_mlp_set_params": ([_vp, _vp], _i),
     "swcs_mlp_get_params": ([_vp, _vp], _i),
     "swcs_mlp_forward_dev": ([_vp, _vp, _i64, _vp], _i),
+    "swcs_mlp_predict_dev": ([_vp, _vp, _i64, _vp], _i),
     "swcs_mlp_grad_dev": ([_vp, _vp, _vp, _i64, _vp, _vp], _i),
     "swcs_mlp_train_step_dev": ([_vp, _vp, _vp, _i64, ctypes.c_float, _vp], _i),
     "swcs_mlp_activations": ([_vp, _vp, _vp, _vp, _i64], _i),
@@ -201,6 +202,10 @@ class Mlp:
 
     def forward_dev(self, d_x, d_y):
         self._ck(lib.swcs_mlp_forward_dev(self._h, _tptr(d_x), int(d_x.shape[0]), _tptr(d_y)))
+
+    def predict_dev(self, d_x, d_y):
+        """Same y as forward_dev from the fused single-kernel forward (no stored activations)."""
+        self._ck(lib.swcs_mlp_predict_dev(self._h, _tptr(d_x), int(d_x.shape[0]), _tptr(d_y)))
 
     def grad_dev(self, d_x, d_t, d_grad, d_loss):
         self._ck(lib.swcs_mlp_grad_dev(self._h, _tptr(d_x), _tptr(d_t), int(d_x.shape[0]), _tptr(d_grad),

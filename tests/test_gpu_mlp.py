@@ -123,3 +123,28 @@ def test_training_reduces_loss(S):
             losses.append(d_loss.item())
     assert losses[1] < 0.2 * losses[0]
     net.close()
+
+
+@pytest.mark.parametrize("n,d_in,width", [(5, 32, 256), (1000, 32, 256), (128 * 152 * 3 + 77, 32, 256),
+                                          (4099, 64, 128), (777, 32, 64), (300, 64, 256)])
+def test_fused_forward_is_bit_identical(S, n, d_in, width):
+    """The fused inference kernel (TMA, both layers on chip) returns exactly the
+    layer-by-layer result, for partial tiles, several tiles per CTA and other
+    shapes (64 x 256 exceeds its shared memory and runs layer by layer)."""
+    import torch
+    rng = np.random.default_rng(n + d_in)
+    net = S.Mlp(d_in, width)
+    flat = he_params(rng, d_in, width)
+    net.set_params(flat)
+    x = M.bf16_round(rng.normal(size=(n, d_in)))
+    d_x = torch.from_numpy(M.bf16_bits(x).view(np.int16).copy()).cuda()
+    y_ref = torch.empty(n, dtype=torch.float32, device="cuda")
+    y = torch.full((n,), float("nan"), dtype=torch.float32, device="cuda")
+    net.forward_dev(d_x, y_ref)
+    net.predict_dev(d_x, y)
+    net.sync()
+    assert torch.equal(y, y_ref)
+    P = unpack(net, flat)
+    ref = M.forward(x, M.bf16_round(P["W1"]), P["b1"], M.bf16_round(P["W2"]), P["b2"], M.bf16_round(P["w3"]),
+                    P["b3"])["y"]
+    assert np.abs(y.cpu().numpy() - ref).max() <= 1e-2 * max(1.0, np.abs(ref).max())
