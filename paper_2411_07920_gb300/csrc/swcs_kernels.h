@@ -217,6 +217,13 @@ struct MlpParams {
   __nv_bfloat16* w3b;
 };
 cudaError_t launch_mlp_gemm(const GemmArgs& g, cudaStream_t st);
+// The w3 dot product of the last layer is summed as kDotGroups partial sums over
+// consecutive 16-column chunks (chunk c of n belongs to group g when
+// dot_group_begin(g, n) <= c < dot_group_begin(g + 1, n)), combined as
+// ((p0 + p1) + p2) + p3; the fused kernel gives each group its own warps, the
+// layer-by-layer kernel sums the same way, so both round identically.
+constexpr int kDotGroups = 4;
+__host__ __device__ __forceinline__ int dot_group_begin(int g, int nchunks) { return g * nchunks / kDotGroups; }
 // Fused inference forward (all three layers in one persistent tcgen05 kernel).
 struct FusedArgs {
   int64_t M;                // rows (pool operators)

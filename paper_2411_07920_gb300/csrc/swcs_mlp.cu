@@ -157,11 +157,14 @@ __global__ void __launch_bounds__(kGemmThreads) mlp_gemm_kernel(GemmArgs g) {
   // ---------------- epilogue: thread t owns row m0 + t (TMEM lane t)
   const int row = m0 + threadIdx.x;
   const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-  float dot = 0.f;
+  float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;  // dot-product partial sums (kDotGroups)
   if (ok) {
     for (int c0 = 0; c0 < g.N; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
+      int grp = 0;
+      while (grp < kDotGroups - 1 && dot_group_begin(grp + 1, g.N / 16) <= c0 / 16) ++grp;
+      float part = grp == 0 ? p0 : (grp == 1 ? p1 : (grp == 2 ? p2 : p3));
       if (row < g.M) {
         if (g.mode == kGemmF32) {
           float* o = g.out_f32 + (size_t)row * g.ldo + c0;
@@ -175,13 +178,17 @@ __global__ void __launch_bounds__(kGemmThreads) mlp_gemm_kernel(GemmArgs g) {
             z = z > 0.f ? z : 0.f;
             const __nv_bfloat16 hb = __float2bfloat16_rn(z);
             o[i] = hb;
-            if (g.mode == kGemmReluBf16Dot) dot += __bfloat162float(hb) * __bfloat162float(g.w3[c0 + i]);
+            if (g.mode == kGemmReluBf16Dot) part += __bfloat162float(hb) * __bfloat162float(g.w3[c0 + i]);
           }
         }
       }
+      if (grp == 0) p0 = part;
+      else if (grp == 1) p1 = part;
+      else if (grp == 2) p2 = part;
+      else p3 = part;
     }
   }
-  if (g.mode == kGemmReluBf16Dot && row < g.M && ok) g.y[row] = dot + g.b3;
+  if (g.mode == kGemmReluBf16Dot && row < g.M && ok) g.y[row] = (((p0 + p1) + p2) + p3) + g.b3;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));

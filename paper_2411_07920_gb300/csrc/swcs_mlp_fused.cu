@@ -1,11 +1,13 @@
 // Screening network, inference: the whole forward pass y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3 of
 // every pool operator in one persistent kernel on the 5th-generation tensor cores.
 //
-//   - one CTA per SM (192 threads, about 225 KB of shared memory), looping over 128-row tiles;
+//   - one CTA per SM (576 threads, about 226 KB of shared memory), looping over 128-row tiles;
 //   - the weights W1 [W x D] and W2 [W x W] are loaded once per CTA by TMA and stay in shared memory;
 //     feature tiles X [128 x D] stream in by TMA through two stages;
-//   - warp 0 (one thread) issues the TMA loads, warp 1 (one thread) the tcgen05.mma, warps 2-5 run the
-//     epilogues; all hand-offs go through mbarriers with bounded waits;
+//   - warp 0 (one thread) issues the TMA loads, warp 1 (one thread) the tcgen05.mma, warps 2-17 run the
+//     epilogues: four warps per group of columns, one per tensor-memory lane quadrant, so every SM
+//     sub-partition has four epilogue warps to hide tensor-memory and shared-memory latency; all hand-offs
+//     go through mbarriers with bounded waits;
 //   - layer 1 accumulates X W1^T into tensor memory columns [0, W), its epilogue writes
 //     H1 = bf16(relu(. + b1)) straight into shared memory in the operand layout of layer 2, and layer 2
 //     accumulates H1 W2^T into columns [256, 256 + W); the second epilogue applies b2, ReLU, BF16 and the
@@ -28,13 +30,15 @@ namespace swcs {
 
 namespace {
 
-constexpr int kFusedThreads = 192;
+constexpr int kEpiThreads = 128 * kDotGroups;  // warps 2 .. 2 + 4 kDotGroups - 1
+constexpr int kFusedThreads = 64 + kEpiThreads;
+constexpr int kCtrlBytes = 256;                 // control block, then the dot-product partials
 constexpr int kTile = 128;
 constexpr uint32_t kT2Col = 256;  // tensor-memory column of the layer-2 accumulator
 constexpr uint64_t kSpinLimit = 1ull << 26;
 
 struct FusedCtrl {
-  uint64_t full_x[2], empty_x[2], w_full, mma1, mma2, t1_free, h1_ready, t2_free, fin;
+  uint64_t full_x[2], empty_x[2], w_full, mma1, mma2, t1_free, h1_ready, t2_free, part_ready, fin;
   uint32_t tmem;
 };
 
@@ -126,7 +130,8 @@ __device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 
 }  // namespace
 
 size_t mlp_fused_smem_bytes(int d_in, int width) {
-  return 128 /* alignment slack */ + 1024 /* control block */ + (size_t)width * d_in * 2 + (size_t)width * width * 2 +
+  return 128 /* alignment slack */ + kCtrlBytes + (size_t)kDotGroups * kTile * 4 /* partials */ +
+         (size_t)width * d_in * 2 + (size_t)width * width * 2 +
          2 * (size_t)kTile * d_in * 2 + (size_t)kTile * width * 2;
 }
 
@@ -138,7 +143,8 @@ mlp_fused_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant
   uint8_t* sm = dsm + pad;
   FusedCtrl& c = *reinterpret_cast<FusedCtrl*>(sm);
   const int D = f.d_in, W = f.width;
-  uint8_t* sW1 = sm + 1024;
+  float* sPart = reinterpret_cast<float*>(sm + kCtrlBytes);  // [kDotGroups][kTile]
+  uint8_t* sW1 = sm + kCtrlBytes + kDotGroups * kTile * 4;
   uint8_t* sW2 = sW1 + (size_t)W * D * 2;
   uint8_t* sX0 = sW2 + (size_t)W * W * 2;
   uint8_t* sX1 = sX0 + (size_t)kTile * D * 2;
@@ -158,9 +164,10 @@ mlp_fused_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant
     mbar_init(&c.w_full, 1);
     mbar_init(&c.mma1, 1);
     mbar_init(&c.mma2, 1);
-    mbar_init(&c.t1_free, 128);
-    mbar_init(&c.h1_ready, 128);
-    mbar_init(&c.t2_free, 128);
+    mbar_init(&c.t1_free, kEpiThreads);
+    mbar_init(&c.h1_ready, kEpiThreads);
+    mbar_init(&c.t2_free, kEpiThreads);
+    mbar_init(&c.part_ready, kEpiThreads);
     mbar_init(&c.fin, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -222,15 +229,17 @@ mlp_fused_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant
       mma_commit(&c.fin);  // every MMA issued above has completed once this phase completes
       if (!mbar_wait_bounded(&c.fin, 0)) bad = true;
     }
-  } else {  // ------------------------------------------------------------ epilogue, warps 2-5
-    const int q = warp & 3;  // a warp reads the tensor-memory lanes 32 (warp % 4) .. + 31
+  } else {  // ------------------------------------------------------------ epilogue, warps 2-17
+    const int q = warp & 3;            // a warp reads the tensor-memory lanes 32 (warp % 4) .. + 31
+    const int grp = (warp - 2) >> 2;   // its group of 16-column chunks
     const int r = q * 32 + lane;
     const uint32_t lanes = (uint32_t)(q * 32) << 16;
+    const int cb = dot_group_begin(grp, W / 16) * 16, ce = dot_group_begin(grp + 1, W / 16) * 16;
     int j = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
       if (!mbar_wait_bounded(&c.mma1, (uint32_t)j & 1u)) { bad = true; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      for (int c0 = 0; c0 < W; c0 += 16) {
+      for (int c0 = cb; c0 < ce; c0 += 16) {
         float v[16];
         tmem_load16(tmem + lanes + (uint32_t)c0, v);
         uint32_t w[8];
@@ -253,8 +262,8 @@ mlp_fused_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant
       mbar_arrive(&c.h1_ready);
       if (!mbar_wait_bounded(&c.mma2, (uint32_t)j & 1u)) { bad = true; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      float dot = 0.f;
-      for (int c0 = 0; c0 < W; c0 += 16) {
+      float part = 0.f;
+      for (int c0 = cb; c0 < ce; c0 += 16) {
         float v[16];
         tmem_load16(tmem + lanes + kT2Col + (uint32_t)c0, v);
 #pragma unroll
@@ -262,13 +271,23 @@ mlp_fused_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant
           float z = v[i] + __ldg(&f.b2[c0 + i]);
           z = z > 0.f ? z : 0.f;
           const __nv_bfloat16 hb = __float2bfloat16_rn(z);
-          dot += __bfloat162float(hb) * __bfloat162float(f.w3[c0 + i]);
+          part += __bfloat162float(hb) * __bfloat162float(f.w3[c0 + i]);
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(&c.t2_free);
-      const int64_t row = (int64_t)t * kTile + r;
-      if (row < f.M) f.y[row] = dot + __ldg(f.b3);
+      // partials of the row meet in shared memory; group 0 adds them in group order.  Group 0 reads
+      // them before it arrives on h1_ready of the next tile, so no group can overwrite them earlier.
+      sPart[grp * kTile + r] = part;
+      mbar_arrive(&c.part_ready);
+      if (grp == 0) {
+        if (!mbar_wait_bounded(&c.part_ready, (uint32_t)j & 1u)) { bad = true; break; }
+        float dot = sPart[r];
+#pragma unroll
+        for (int gg = 1; gg < kDotGroups; ++gg) dot += sPart[gg * kTile + r];
+        const int64_t row = (int64_t)t * kTile + r;
+        if (row < f.M) f.y[row] = dot + __ldg(f.b3);
+      }
     }
   }
   if (bad && f.err) set_error(f.err, kDevTimeout);

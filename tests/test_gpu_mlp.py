@@ -126,7 +126,8 @@ def test_training_reduces_loss(S):
 
 
 @pytest.mark.parametrize("n,d_in,width", [(5, 32, 256), (1000, 32, 256), (128 * 152 * 3 + 77, 32, 256),
-                                          (4099, 64, 128), (777, 32, 64), (300, 64, 256)])
+                                          (4099, 64, 128), (777, 32, 64), (300, 64, 256),
+                                          (301600, 32, 256)])
 def test_fused_forward_is_bit_identical(S, n, d_in, width):
     """The fused inference kernel (TMA, both layers on chip) returns exactly the
     layer-by-layer result, for partial tiles, several tiles per CTA and other
