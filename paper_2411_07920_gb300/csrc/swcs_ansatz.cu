@@ -66,7 +66,8 @@ enum { kCtrExtra = 0, kCtrZero = 1, kCtrKept = 2, kCtrN = 4 };
 
 }  // namespace
 
-__global__ void __launch_bounds__(kAnsatzThreads)
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads)
 ansatz_kernel(AnsatzArgs a) {
   __shared__ SelState sel;
   __shared__ unsigned s_hist[256];
@@ -297,25 +298,32 @@ ansatz_kernel(AnsatzArgs a) {
   }
 }
 
-int ansatz_blocks_per_sm() {
+// One 1024-thread CTA per SM for a single state (fewest CTAs at the grid
+// barriers); 256-thread CTAs where many instances share the device (several
+// instances' CTAs can then be resident on one SM).
+int ansatz_blocks_per_sm(int threads) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ansatz_kernel, kAnsatzThreads, 0) != cudaSuccess) return 0;
-  return nb;
+  const cudaError_t e = threads == kAnsatzThreadsShared
+                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ansatz_kernel<kAnsatzThreadsShared>, threads, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ansatz_kernel<kAnsatzThreads>, threads, 0);
+  return e == cudaSuccess ? nb : 0;
 }
 
-cudaError_t launch_ansatz(const AnsatzArgs& args, int nblocks, cudaStream_t st) {
+cudaError_t launch_ansatz(const AnsatzArgs& args, int nblocks, int threads, cudaStream_t st) {
+  if (threads != kAnsatzThreads && threads != kAnsatzThreadsShared) return cudaErrorInvalidValue;
   // cooperative launch (all CTAs co-resident, as the grid barrier needs); the
   // launch-attribute form is also valid inside stream capture
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nblocks);
-  cfg.blockDim = dim3(kAnsatzThreads);
+  cfg.blockDim = dim3(threads);
   cfg.stream = st;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeCooperative;
   at[0].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, ansatz_kernel, args);
+  if (threads == kAnsatzThreadsShared) return cudaLaunchKernelEx(&cfg, ansatz_kernel<kAnsatzThreadsShared>, args);
+  return cudaLaunchKernelEx(&cfg, ansatz_kernel<kAnsatzThreads>, args);
 }
 
 }  // namespace swcs

@@ -70,6 +70,7 @@ struct swcs_ctx {
   int opt_skip_arrive = -1;              // test hook (see swcs_set_option)
   uint64_t opt_ext_cap = 0;              // hashed sweep: first table capacity (0: sized from an estimate)
   int opt_gate_blocks = 0;   // CTAs of the gate kernel (0: whole device)
+  int opt_gate_threads = kAnsatzThreads;  // threads per gate-kernel CTA (batched instances: kAnsatzThreadsShared)
   int opt_row_clusters = 0;  // clusters of the row sweep (0: as many as fit)
 
   // adjoint: checkpoints, per-gate snapshots of one segment, sigma, nu, indices, gradient
@@ -353,7 +354,8 @@ int64_t max_state_for(swcs_ctx* c, int64_t n_keep, int n_ops, int64_t n_now) {
 int run_gates(swcs_ctx* c, const uint8_t* d_ops, const double* d_cs, int n_ops, int64_t n_keep, bool reset,
               uint64_t* snap_keys = nullptr, double* snap_amps = nullptr, long long* snap_n = nullptr,
               int64_t snap_stride = 0, bool keep_zeros = false) {
-  const int bps = ansatz_blocks_per_sm();
+  const int gthreads = c->opt_gate_threads;
+  const int bps = ansatz_blocks_per_sm(gthreads);
   if (bps <= 0) return fail(c, SWCS_ERR_NO_DEVICE, "ansatz kernel cannot be resident on this device");
   AnsatzArgs a{};
   a.keys_a = (uint64_t*)c->keys_a.p;
@@ -394,7 +396,7 @@ int run_gates(swcs_ctx* c, const uint8_t* d_ops, const double* d_cs, int n_ops, 
   CK(cudaMemsetAsync(&k->bar, 0, sizeof(GridBar), c->st));
   int nblocks = c->nsm * bps;
   if (c->opt_gate_blocks > 0) nblocks = std::min(nblocks, c->opt_gate_blocks);
-  CK(launch_k(c, kKAnsatz, [&] { return launch_ansatz(a, nblocks, c->st); }));
+  CK(launch_k(c, kKAnsatz, [&] { return launch_ansatz(a, nblocks, gthreads, c->st); }));
   c->tab_cur = (int)(((unsigned)n_ops) & 1u);  // the kernel rebuilds tab[0] for the input, swaps per gate
   c->have_state = true;
   c->n_state_host = -1;
@@ -1465,9 +1467,10 @@ int batch_capture(swcs_batch* b, double share, int cluster) {
   std::vector<double> w(n);
   for (int i = 0; i < n; ++i) wsum += (w[i] = inst_work(b->inst[i], b->n_ops[i], b->max_state[i]));
   swcs_ctx* c0 = b->inst[0];
-  const int gate_total = c0->nsm * std::max(1, ansatz_blocks_per_sm());
+  const int gate_total = c0->nsm * std::max(1, ansatz_blocks_per_sm(kAnsatzThreadsShared));
   for (int i = 0; i < n; ++i) {
     swcs_ctx* c = b->inst[i];
+    c->opt_gate_threads = kAnsatzThreadsShared;
     const double f = std::min(1.0, share * w[i] / wsum);
     c->opt_gate_blocks = std::max(1, (int)std::lround(f * gate_total));
     c->opt_cluster = cluster;
@@ -1598,7 +1601,7 @@ int swcs_batch_build(swcs_batch* b, int autotune) {
   if (!autotune) return batch_capture(b, b->share, b->cluster);
   // autotuner: device share per unit of work and cluster size of the row
   // sweep, timed on the whole graph
-  const double shares[] = {1.0, 2.0, 4.0, 8.0};
+  const double shares[] = {1.0, 2.0, 4.0, 8.0, 16.0, 32.0};
   const int clusters[] = {1, 2};
   double best_ms = 1e30, best_share = 1.0;
   int best_cl = 2;

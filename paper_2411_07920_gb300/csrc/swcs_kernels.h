@@ -10,7 +10,8 @@
 
 namespace swcs {
 
-constexpr int kAnsatzThreads = 1024;
+constexpr int kAnsatzThreads = 1024;        // gate kernel CTA, one state on the device
+constexpr int kAnsatzThreadsShared = 256;   // gate kernel CTA, instances sharing the device
 constexpr int kSigmaThreads = 256;
 constexpr int kMaxSpin = 32;  // spin-orbitals of one spin (n_so <= 64)
 
@@ -46,8 +47,8 @@ struct AnsatzArgs {
   int skip_arrive_block;  // test hook: this CTA never arrives at its first grid barrier (-1: off)
 };
 
-int ansatz_blocks_per_sm();
-cudaError_t launch_ansatz(const AnsatzArgs& a, int nblocks, cudaStream_t st);
+int ansatz_blocks_per_sm(int threads);
+cudaError_t launch_ansatz(const AnsatzArgs& a, int nblocks, int threads, cudaStream_t st);
 
 // Hamiltonian and pool tables on the device.
 struct HamDev {
