@@ -273,7 +273,21 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
     warp_lists(sh, warp, lane, d, m);
     const uint8_t* oa = sh.occ_all[warp];
     const int pa = en.o[0], pb = en.o[2];  // alpha spin-orbitals: removed, added
-    if (lane == 0) row_pair<SCATTER>(A, row, touched, d, cd, A.grank[di], pa, -1, pb, -1, oa);
+    if (SCATTER) {  // the alpha single itself: its Fock element summed across the warp
+      const int n = A.H.n;
+      const double* w = A.H.Ws + ((size_t)pa * n + pb) * n;
+      double f = 0.0;
+      for (int t3 = lane; t3 < A.H.ne; t3 += 32) f += w[oa[t3]];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+      if (lane == 0) {
+        const uint32_t rd = A.grank[di];
+        atomicAdd(&row[rd], apply_sign(A.H.h[pb * n + pa] + f, single_phase(d, pa, pb)) * cd);
+        mark(touched, rd);
+      }
+    } else if (lane == 0) {
+      row_pair<SCATTER>(A, row, touched, d, cd, A.grank[di], pa, -1, pb, -1, oa);
+    }
     // alpha-beta doubles: phase = (beta single on D) ^ (alpha single on D) ^ (index-only bit in the tables)
     const int sa = single_phase(d, pa, pb);
     const size_t base = ((size_t)(pa >> 1) * m + (pb >> 1)) * (size_t)m * m;
