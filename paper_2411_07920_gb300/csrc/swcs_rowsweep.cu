@@ -95,26 +95,32 @@ __device__ __forceinline__ double fock_single(const RowArgs& A, const uint8_t* o
   return f;
 }
 
-// Entries receive several contributions: the atomic is issued only while the
-// bit still reads as clear (two lanes that both see it clear both set it).
-__device__ __forceinline__ void mark(unsigned* touched, uint32_t i) {
-  if (touched) {
-    const unsigned bit = 1u << (i & 31);
-    if (!(touched[i >> 5] & bit)) atomicOr(&touched[i >> 5], bit);
-  }
+// Whether a scatter to row entry i is needed, recording the entry as touched.
+// Entries receive several contributions: the bit is set atomically only while
+// it still reads as clear (two lanes that both see it clear both set it).  In
+// energy-only mode (filt) only the entries of X's own determinants are read
+// back: their bits are set before the scatter, every other entry is skipped.
+__device__ __forceinline__ bool take(unsigned* touched, bool filt, uint32_t i) {
+  if (!touched) return true;
+  const unsigned bit = 1u << (i & 31);
+  const unsigned w = touched[i >> 5];
+  if (filt) return (w & bit) != 0u;
+  if (!(w & bit)) atomicOr(&touched[i >> 5], bit);
+  return true;
 }
 
 // One connected pair, scatter or gather.  (p<q) removed, (r<s) added for
 // doubles; q = s = -1 marks a single p -> r.
 template <bool SCATTER>
-__device__ __forceinline__ void row_pair(const RowArgs& A, double* row, unsigned* touched, uint64_t d, double cd,
-                                         uint32_t rank_e, int p, int q, int r, int s, const uint8_t* occ_all) {
+__device__ __forceinline__ void row_pair(const RowArgs& A, double* row, unsigned* touched, bool filt, uint64_t d,
+                                         double cd, uint32_t rank_e, int p, int q, int r, int s,
+                                         const uint8_t* occ_all) {
   const int n = A.H.n;
   if (q < 0) {
     if (SCATTER) {
+      if (!take(touched, filt, rank_e)) return;
       const int sb = single_phase(d, p, r);
       atomicAdd(&row[rank_e], apply_sign(fock_single(A, occ_all, p, r), sb) * cd);
-      mark(touched, rank_e);
     } else {
       const int lo = p < r ? p : r, hi = p < r ? r : p;
       const int k = A.H.ops1[lo * n + hi];
@@ -126,9 +132,9 @@ __device__ __forceinline__ void row_pair(const RowArgs& A, double* row, unsigned
   }
   const int pa = pair_index(p, q, n), pb = pair_index(r, s, n);
   if (SCATTER) {
+    if (!take(touched, filt, rank_e)) return;
     const int sb = double_phase(d, p, q, r, s);
     atomicAdd(&row[rank_e], apply_sign(A.H.G[(size_t)pa * A.H.npairs + pb], sb) * cd);
-    mark(touched, rank_e);
   } else {
     const bool down = pa > pb;
     const int k = down ? A.H.opd[(size_t)pb * A.H.npairs + pa] : A.H.opd[(size_t)pa * A.H.npairs + pb];
@@ -204,6 +210,7 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
   const int t_same = 1 + ks * nvs + (ks * (ks - 1) / 2) * n_tv;
   const int nch = (t_same + kSameChunk - 1) / kSameChunk;
   unsigned* touched = SCATTER ? dy.touched : nullptr;
+  const bool filt = SCATTER && A.energy_only && dy.touched != nullptr;
   // ---------------- X's own group: diagonal, beta singles, beta-beta doubles; items (determinant, chunk)
   const long long n_items_same = sh.gx_cnt * nch;
   for (long long u = (long long)crank * kRowWarps + warp; u < n_items_same; u += (long long)gsz * kRowWarps) {
@@ -228,8 +235,7 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
       if (lane == 0) {
         const uint32_t rd = A.grank[di];
         if (SCATTER) {
-          atomicAdd(&row[rd], hd * cd);
-          mark(touched, rd);
+          if (take(touched, filt, rd)) atomicAdd(&row[rd], hd * cd);
         } else {
           e_acc += cd * row[rd];
         }
@@ -246,8 +252,7 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
         const int sb = (int)(wb >> 31);
         const int p = 2 * i + 1, r = 2 * jv + 1;
         if (SCATTER) {
-          atomicAdd(&row[re], apply_sign(fock_single(A, oa, p, r), sb) * cd);
-          mark(touched, re);
+          if (take(touched, filt, re)) atomicAdd(&row[re], apply_sign(fock_single(A, oa, p, r), sb) * cd);
         } else {
           const int k = A.H.ops1[(p < r ? p : r) * A.H.n + (p < r ? r : p)];
           if (!A.sel_bits || ((__ldg(&A.sel_bits[k >> 5]) >> (k & 31)) & 1u))
@@ -257,7 +262,7 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
         const int i1 = sh.bocc[warp][o1], i2 = sh.bocc[warp][o2];
         const int j1 = sh.bvir[warp][v1], j2 = sh.bvir[warp][v2];
         const uint32_t re = str_rank(A.rank_tab, ks, db ^ (1u << i1) ^ (1u << i2) ^ (1u << j1) ^ (1u << j2));
-        row_pair<SCATTER>(A, row, touched, d, cd, re, 2 * i1 + 1, 2 * i2 + 1, 2 * j1 + 1, 2 * j2 + 1, oa);
+        row_pair<SCATTER>(A, row, touched, filt, d, cd, re, 2 * i1 + 1, 2 * i2 + 1, 2 * j1 + 1, 2 * j2 + 1, oa);
       }
     }
     __syncwarp();
@@ -274,19 +279,19 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
     const uint8_t* oa = sh.occ_all[warp];
     const int pa = en.o[0], pb = en.o[2];  // alpha spin-orbitals: removed, added
     if (SCATTER) {  // the alpha single itself: its Fock element summed across the warp
-      const int n = A.H.n;
-      const double* w = A.H.Ws + ((size_t)pa * n + pb) * n;
-      double f = 0.0;
-      for (int t3 = lane; t3 < A.H.ne; t3 += 32) f += w[oa[t3]];
+      const uint32_t rd = A.grank[di];
+      if (!filt || ((touched[rd >> 5] >> (rd & 31)) & 1u)) {  // the same word for every lane
+        const int n = A.H.n;
+        const double* w = A.H.Ws + ((size_t)pa * n + pb) * n;
+        double f = 0.0;
+        for (int t3 = lane; t3 < A.H.ne; t3 += 32) f += w[oa[t3]];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
-      if (lane == 0) {
-        const uint32_t rd = A.grank[di];
-        atomicAdd(&row[rd], apply_sign(A.H.h[pb * n + pa] + f, single_phase(d, pa, pb)) * cd);
-        mark(touched, rd);
+        for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+        if (lane == 0 && take(touched, filt, rd))
+          atomicAdd(&row[rd], apply_sign(A.H.h[pb * n + pa] + f, single_phase(d, pa, pb)) * cd);
       }
     } else if (lane == 0) {
-      row_pair<SCATTER>(A, row, touched, d, cd, A.grank[di], pa, -1, pb, -1, oa);
+      row_pair<SCATTER>(A, row, touched, filt, d, cd, A.grank[di], pa, -1, pb, -1, oa);
     }
     // alpha-beta doubles: phase = (beta single on D) ^ (alpha single on D) ^ (index-only bit in the tables)
     const int sa = single_phase(d, pa, pb);
@@ -294,13 +299,23 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
     const uint32_t* rb = A.rbeta + (size_t)di * (ks * nvs);
     const int nsb = ks * nvs;
     if (SCATTER) {
-      for (int t2 = lane; t2 < nsb; t2 += 32) {
-        const int i = sh.bocc[warp][t2 / nvs], j = sh.bvir[warp][t2 % nvs];
-        const uint32_t wb = __ldg(&rb[t2]);
-        const uint32_t re = wb & 0x7FFFFFFFu;
-        const int sb = (int)(wb >> 31) ^ sa;
-        atomicAdd(&row[re], apply_sign(__ldg(&A.gab[base + (size_t)i * m + j]), sb) * cd);
-        mark(touched, re);
+      if (filt) {  // energy only: almost every target is skipped, so test before loading the integral
+        for (int t2 = lane; t2 < nsb; t2 += 32) {
+          const uint32_t wb = __ldg(&rb[t2]);
+          const uint32_t re = wb & 0x7FFFFFFFu;
+          if (!take(touched, true, re)) continue;
+          const int i = sh.bocc[warp][t2 / nvs], j = sh.bvir[warp][t2 % nvs];
+          atomicAdd(&row[re], apply_sign(__ldg(&A.gab[base + (size_t)i * m + j]), (int)(wb >> 31) ^ sa) * cd);
+        }
+      } else {  // both loads issued up front, off the atomic's dependency chain
+        for (int t2 = lane; t2 < nsb; t2 += 32) {
+          const int i = sh.bocc[warp][t2 / nvs], j = sh.bvir[warp][t2 % nvs];
+          const uint32_t wb = __ldg(&rb[t2]);
+          const double gv = __ldg(&A.gab[base + (size_t)i * m + j]);
+          const uint32_t re = wb & 0x7FFFFFFFu;
+          take(touched, false, re);
+          atomicAdd(&row[re], apply_sign(gv, (int)(wb >> 31) ^ sa) * cd);
+        }
       }
     } else {
       // four targets per lane with their row reads issued together
@@ -346,7 +361,7 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
       while (e + 1 < sh.n_d && dy.ents_d[e + 1].flat <= t) ++e;
       const RowEnt en = dy.ents_d[e];
       const long long di = A.goff[en.gid] + (t - en.flat);
-      row_pair<SCATTER>(A, row, touched, A.gkey[di], A.gamp[di], A.grank[di], en.o[0], en.o[1], en.o[2], en.o[3],
+      row_pair<SCATTER>(A, row, touched, filt, A.gkey[di], A.gamp[di], A.grank[di], en.o[0], en.o[1], en.o[2], en.o[3],
                         nullptr);
     }
   }
@@ -419,6 +434,12 @@ row_sweep_kernel(RowArgs A) {
     }
     __syncthreads();
     if (A.energy_only && sh.gx_cnt == 0) continue;  // same decision in every CTA of the cluster
+    if (A.energy_only && dy.touched) {  // the entries that will be read back: X's own determinants
+      for (long long t = threadIdx.x; t < sh.gx_cnt; t += kRowThreads) {
+        const uint32_t rk = A.grank[sh.gx_off + t];
+        atomicOr(&dy.touched[rk >> 5], 1u << (rk & 31));
+      }
+    }
     // candidates c = 0 .. ns+nd-1 (alpha singles then doubles of X); this CTA takes c = crank (mod gsz)
     for (int cc = threadIdx.x; crank + cc * gsz < ns + nd; cc += kRowThreads) {
       const int c = crank + cc * gsz;
