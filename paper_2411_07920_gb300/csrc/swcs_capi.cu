@@ -569,6 +569,7 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
   ra.energy_only = energy_only ? 1 : 0;
   ra.sig_out = sig_out;
   ra.gorig = (const uint32_t*)c->gorig.p;
+  ra.n_groups = ga.n_groups;
   CK(launch_k(c, kKRow, [&] { return launch_row_sweep(ra, nthr, c->opt_row_occ, gsz, ncl, smem, c->st); }));
   c->stats[2] = 0;
   c->stats[3] = ncl;

@@ -138,6 +138,7 @@ struct RowArgs {
   int energy_only;
   double* sig_out;
   const uint32_t* gorig;
+  const unsigned long long* n_groups;  // groups of the state (energy only: the targets are these alpha strings)
 };
 
 struct GroupArgs {

@@ -414,8 +414,11 @@ row_sweep_kernel(RowArgs A) {
   double e_acc = 0.0;
   __syncthreads();
 
-  for (int xi = cid; xi < A.NA; xi += ncl) {
-    const uint32_t X = A.alpha_list[xi];
+  // targets: every alpha string of the sector, or in energy-only mode the alpha strings of the state's
+  // groups (the others hold no determinant whose sigma is read back)
+  const int n_targets = A.energy_only ? (int)*A.n_groups : A.NA;
+  for (int xi = cid; xi < n_targets; xi += ncl) {
+    const uint32_t X = A.energy_only ? even_bits(A.gkey[A.goff[xi]]) : A.alpha_list[xi];
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
       const bool inr = lane < m;
@@ -427,7 +430,7 @@ row_sweep_kernel(RowArgs A) {
       if (lane == 0) {
         sh.n_s = 0;
         sh.n_d = 0;
-        const int64_t g = idx_lookup(A.atab, A.amask, (uint64_t)X);
+        const int64_t g = A.energy_only ? (int64_t)xi : idx_lookup(A.atab, A.amask, (uint64_t)X);
         sh.gx_off = g >= 0 ? A.goff[g] : 0;
         sh.gx_cnt = g >= 0 ? A.goff[g + 1] - A.goff[g] : 0;
       }
