@@ -236,3 +236,27 @@ def test_so28_e8_full_size(S):
     c.set_option("sweep", 1)
     g1 = c.pool_gradients()
     assert np.abs(g1 - g).max() < TOL
+
+
+@pytest.mark.parametrize("n_e,n_keep,sweep", [(4, 300, 0), (6, 200, 0), (4, 300, 1)])
+def test_largest_orbital_space(S, n_e, n_keep, sweep):
+    """64 spin-orbitals, the largest the bitstrings hold: determinants with bit 63 set, the
+    708,784-operator pool, 32-orbital alpha strings in the row sweep (sweep 0) and the hashed
+    external table (sweep 1)."""
+    w = I.small_case(64, n_e, 24, 140 + n_e, n_keep=n_keep)
+    top = np.array([[2, 0, 1, 62, 63], [1, n_e - 1, 63, 0, 0]], np.uint8)
+    ops = np.concatenate([w.ops, top])
+    theta = np.concatenate([w.theta, [0.4, -0.3]])
+    c = ctx_for(S, w)
+    c.set_option("sweep", sweep)
+    c.apply_ansatz(ops, theta, n_keep)
+    k, a = c.get_state()
+    ko, ao = O.apply_ansatz(64, n_e, ops, theta, n_keep)
+    assert_state_equal(k, a, ko, ao)
+    assert (ko >> np.uint64(63)).any()
+    e, _ = c.energy()
+    assert abs(e - O.energy(64, w.h, w.g, ko, ao)[0]) < TOL
+    g = c.pool_gradients()
+    go = O.pool_gradients(64, w.h, w.g, ko, ao)
+    assert len(go) == 708784
+    assert np.abs(g - go).max() < TOL
