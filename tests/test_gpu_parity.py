@@ -260,3 +260,21 @@ def test_largest_orbital_space(S, n_e, n_keep, sweep):
     go = O.pool_gradients(64, w.h, w.g, ko, ao)
     assert len(go) == 708784
     assert np.abs(g - go).max() < TOL
+
+
+@pytest.mark.parametrize("n_so,n_e", [(12, 2), (12, 10), (8, 6), (4, 2)])
+def test_nearly_empty_and_nearly_full_sectors(S, n_so, n_e):
+    """One electron or one hole per spin: no same-spin doubles on one side, so the row sweep's
+    pair tables are empty there; both sweeps and the energy against the oracle."""
+    w = I.small_case(n_so, n_e, 12, 150 + n_so + n_e)
+    ko, ao = O.apply_ansatz(n_so, n_e, w.ops, w.theta, 0)
+    go = O.pool_gradients(n_so, w.h, w.g, ko, ao)
+    eo = O.energy(n_so, w.h, w.g, ko, ao)[0]
+    for sweep in (2, 1):
+        c = ctx_for(S, w)
+        c.set_option("sweep", sweep)
+        c.apply_ansatz(w.ops, w.theta, 0)
+        k, a = c.get_state()
+        assert_state_equal(k, a, ko, ao)
+        assert abs(c.energy()[0] - eo) < TOL
+        assert np.abs(c.pool_gradients() - go).max() < TOL
