@@ -60,8 +60,8 @@ __device__ __forceinline__ uint32_t str_rank(const uint32_t* __restrict__ T, int
 }
 
 struct RowEnt {
-  uint32_t gid;
-  uint32_t flat;  // exclusive prefix of work items within its list
+  uint32_t off;   // first determinant of the group (grouped order)
+  uint32_t flat;  // the group's size when found; then the exclusive prefix of work items within its list
   uint8_t o[4];   // spin-orbitals removed from D (o[0], o[1]) and added (o[2], o[3]); singles use o[0], o[2]
 };
 
@@ -161,13 +161,10 @@ __device__ __forceinline__ void warp_lists(RowShared& sh, int warp, int lane, ui
 // Block-wide exclusive scan, in list order, of the work items of each entry:
 // ceil(group size / chunk).
 template <int kRowThreads>
-__device__ void scan_items(RowShared& sh, RowEnt* ents, int cnt, const long long* goff, int chunk, uint32_t* total) {
+__device__ void scan_items(RowShared& sh, RowEnt* ents, int cnt, int chunk, uint32_t* total) {
   const int per = (cnt + kRowThreads - 1) / kRowThreads;
   const int b = threadIdx.x * per, e = min(cnt, b + per);
-  auto items = [&](int i) {
-    const unsigned sz = (unsigned)(goff[ents[i].gid + 1] - goff[ents[i].gid]);
-    return (sz + chunk - 1) / chunk;
-  };
+  auto items = [&](int i) { return (ents[i].flat + chunk - 1) / chunk; };  // flat still holds the size
   unsigned sum = 0;
   for (int i = b; i < e; ++i) sum += items(i);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -183,8 +180,9 @@ __device__ void scan_items(RowShared& sh, RowEnt* ents, int cnt, const long long
   for (int w = 0; w < warp; ++w) wbase += sh.scan_tmp[w];
   unsigned run = wbase + inc - sum;
   for (int i = b; i < e; ++i) {
+    const unsigned it = items(i);
     ents[i].flat = run;
-    run += items(i);
+    run += it;
   }
   if (threadIdx.x == kRowThreads - 1) *total = run;
   __syncthreads();
@@ -271,7 +269,7 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
   for (uint32_t t = warp; t < sh.tot_s; t += kRowWarps) {
     const int e = find_entry(dy.ents_s, sh.n_s, t);
     const RowEnt en = dy.ents_s[e];
-    const long long di = A.goff[en.gid] + (t - en.flat);
+    const long long di = (long long)en.off + (t - en.flat);
     const uint64_t d = A.gkey[di];
     const double cd = A.gamp[di];
     const uint32_t db = even_bits(d >> 1);
@@ -360,7 +358,7 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
     if (t < sh.tot_d) {
       while (e + 1 < sh.n_d && dy.ents_d[e + 1].flat <= t) ++e;
       const RowEnt en = dy.ents_d[e];
-      const long long di = A.goff[en.gid] + (t - en.flat);
+      const long long di = (long long)en.off + (t - en.flat);
       row_pair<SCATTER>(A, row, touched, filt, A.gkey[di], A.gamp[di], A.grank[di], en.o[0], en.o[1], en.o[2], en.o[3],
                         nullptr);
     }
@@ -464,8 +462,8 @@ row_sweep_kernel(RowArgs A) {
       const int64_t g = idx_lookup(A.atab, A.amask, (uint64_t)Y);
       if (g >= 0) {
         RowEnt en;
-        en.gid = (uint32_t)g;
-        en.flat = 0;
+        en.off = (uint32_t)A.goff[g];
+        en.flat = (uint32_t)(A.goff[g + 1] - A.goff[g]);
         en.o[0] = o4[0]; en.o[1] = o4[1]; en.o[2] = o4[2]; en.o[3] = o4[3];
         if (single) {
           const int slot = atomicAdd(&sh.n_s, 1);
@@ -483,8 +481,8 @@ row_sweep_kernel(RowArgs A) {
       sh.n_d = min(sh.n_d, A.max_ent_d);
     }
     __syncthreads();
-    scan_items<kRowThreads>(sh, dy.ents_s, sh.n_s, A.goff, 1, &sh.tot_s);
-    scan_items<kRowThreads>(sh, dy.ents_d, sh.n_d, A.goff, kDblChunk, &sh.tot_d);
+    scan_items<kRowThreads>(sh, dy.ents_s, sh.n_s, 1, &sh.tot_s);
+    scan_items<kRowThreads>(sh, dy.ents_d, sh.n_d, kDblChunk, &sh.tot_d);
 
     row_phase<kRowThreads, true>(A, sh, dy, row, crank, gsz, e_acc);
     cl.sync();
