@@ -395,7 +395,12 @@ int run_gates(swcs_ctx* c, const uint8_t* d_ops, const double* d_cs, int n_ops, 
   // barrier words must start at zero
   CK(cudaMemsetAsync(&k->bar, 0, sizeof(GridBar), c->st));
   int nblocks = c->nsm * bps;
-  if (c->opt_gate_blocks > 0) nblocks = std::min(nblocks, c->opt_gate_blocks);
+  if (c->opt_gate_blocks > 0) {
+    nblocks = std::min(nblocks, c->opt_gate_blocks);
+  } else {  // small states: about two entries per thread, since every grid barrier costs per CTA
+    const int64_t want = (c->cap + 2 * gthreads - 1) / (2 * gthreads);
+    nblocks = (int)std::max<int64_t>(std::min<int64_t>(nblocks, want), std::min(nblocks, 8));
+  }
   CK(launch_k(c, kKAnsatz, [&] { return launch_ansatz(a, nblocks, gthreads, c->st); }));
   c->tab_cur = (int)(((unsigned)n_ops) & 1u);  // the kernel rebuilds tab[0] for the input, swaps per gate
   c->have_state = true;
