@@ -487,7 +487,7 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
   const int ns = ks * nvs, ndb = (ks * (ks - 1) / 2) * (nvs * (nvs - 1) / 2);
   const int max_s = (ns + gsz - 1) / gsz + 1, max_d = (ndb + gsz - 1) / gsz + 1;
   const int t_same = 1 + ns + ndb;
-  int twords = (int)((c->NB + 31) / 32);
+  int twords = (int)((c->NB + 127) / 128);  // one bit per 32-byte sector (4 entries) of the row
   size_t smem = row_sweep_smem(max_s, max_d, t_same, twords);
   if (smem > 96 * 1024) {  // no room for the touched bitmap: clear whole rows
     twords = 0;
@@ -513,7 +513,7 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
       (r = ensure(c, c->gcount, nd * 8 + 8)) || (r = ensure(c, c->goff, nd * 8 + 16)) ||
       (r = ensure(c, c->gfill, nd * 8 + 8)) || (r = ensure(c, c->gkey, nd * 8 + 8)) ||
       (r = ensure(c, c->gamp, nd * 8 + 8)) || (r = ensure(c, c->grank, nd * 4 + 4)) ||
-      (r = ensure(c, c->rows, (size_t)ncl * c->NB * 8)) ||
+      (r = ensure(c, c->rows, (size_t)ncl * ((c->NB + 3) & ~(int64_t)3) * 8)) ||
       (r = ensure(c, c->rbeta, (size_t)std::max<int64_t>(nd, 1) * ks * nvs * 4)) ||
       (r = ensure(c, c->gorig, (size_t)std::max<int64_t>(nd, 1) * 4)))
     return r;
@@ -524,7 +524,7 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
   CK(cudaMemsetAsync(&k->n_distinct, 0, 8, c->st));
   CK(cudaMemsetAsync(k->acc, 0, 16, c->st));
   if (!energy_only) CK(cudaMemsetAsync(d_g, 0, sizeof(double) * c->pool_size, c->st));
-  CK(cudaMemsetAsync(c->rows.p, 0, (size_t)ncl * c->NB * 8, c->st));
+  CK(cudaMemsetAsync(c->rows.p, 0, (size_t)ncl * ((c->NB + 3) & ~(int64_t)3) * 8, c->st));  // rows padded to 32 B
   GroupArgs ga;
   ga.keys = (const uint64_t*)c->keys_a.p;
   ga.amps = (const double*)c->amps_a.p;

@@ -117,13 +117,13 @@ struct RowArgs {
   const uint32_t* alpha_list;  // every alpha string of the sector
   int NA;
   const uint32_t* rank_tab;    // [4][ks+1][256]
-  double* rows;                // [clusters][NB]
+  double* rows;                // [clusters][NB rounded up to a multiple of 4]
   int64_t NB;
   double* g;
   double* acc;                 // acc[0] += sum c_D sigma_D
   int* err;
   int max_ent_s, max_ent_d;
-  int touched_words;  // words of the per-CTA touched-entry bitmap (0: clear whole rows)
+  int touched_words;  // words of the per-CTA touched-sector bitmap, one bit per 4 entries (0: clear whole rows)
   const uint32_t* sel_bits;  // pool operators to evaluate (nullptr: all)
   // beta single excitations of each grouped determinant, t = occ_slot*nv + vir_slot:
   // rank of the new beta string | (phase bit << 31)

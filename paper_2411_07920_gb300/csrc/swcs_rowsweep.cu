@@ -95,17 +95,23 @@ __device__ __forceinline__ double fock_single(const RowArgs& A, const uint8_t* o
   return f;
 }
 
-// Whether a scatter to row entry i is needed, recording the entry as touched.
-// Entries receive several contributions: the bit is set atomically only while
-// it still reads as clear (two lanes that both see it clear both set it).  In
-// energy-only mode (filt) only the entries of X's own determinants are read
-// back: their bits are set before the scatter, every other entry is skipped.
+// The touched bitmap holds one bit per 32-byte sector (4 entries) of the row:
+// clearing works in whole sectors anyway, and a sector is usually hit by
+// several contributions.
+__device__ __forceinline__ uint32_t sector_word(uint32_t i) { return i >> 7; }
+__device__ __forceinline__ unsigned sector_bit(uint32_t i) { return 1u << ((i >> 2) & 31u); }
+
+// Whether a scatter to row entry i is needed, recording its sector as touched.
+// The bit is set atomically only while it still reads as clear (two lanes that
+// both see it clear both set it).  In energy-only mode (filt) only the sectors
+// of X's own determinants are read back: their bits are set before the
+// scatter, every other sector is skipped.
 __device__ __forceinline__ bool take(unsigned* touched, bool filt, uint32_t i) {
   if (!touched) return true;
-  const unsigned bit = 1u << (i & 31);
-  const unsigned w = touched[i >> 5];
+  const unsigned bit = sector_bit(i);
+  const unsigned w = touched[sector_word(i)];
   if (filt) return (w & bit) != 0u;
-  if (!(w & bit)) atomicOr(&touched[i >> 5], bit);
+  if (!(w & bit)) atomicOr(&touched[sector_word(i)], bit);
   return true;
 }
 
@@ -278,7 +284,7 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
     const int pa = en.o[0], pb = en.o[2];  // alpha spin-orbitals: removed, added
     if (SCATTER) {  // the alpha single itself: its Fock element summed across the warp
       const uint32_t rd = A.grank[di];
-      if (!filt || ((touched[rd >> 5] >> (rd & 31)) & 1u)) {  // the same word for every lane
+      if (!filt || (touched[sector_word(rd)] & sector_bit(rd))) {  // the same word for every lane
         const int n = A.H.n;
         const double* w = A.H.Ws + ((size_t)pa * n + pb) * n;
         double f = 0.0;
@@ -375,7 +381,7 @@ row_sweep_kernel(RowArgs A) {
   const int crank = (int)cl.block_rank();
   const int gsz = (int)cl.num_blocks();
   const int cid = blockIdx.x / gsz, ncl = gridDim.x / gsz;
-  double* row = A.rows + (size_t)cid * A.NB;
+  double* row = A.rows + (size_t)cid * (size_t)((A.NB + 3) & ~(int64_t)3);  // rows padded to whole 32-byte sectors
   const int m = A.H.n >> 1, ks = A.H.no, nvs = A.H.nv;
   const int n_to = ks * (ks - 1) / 2, n_tv = nvs * (nvs - 1) / 2;
   const int ns = ks * nvs, nd = n_to * n_tv;
@@ -438,7 +444,7 @@ row_sweep_kernel(RowArgs A) {
     if (A.energy_only && dy.touched) {  // the entries that will be read back: X's own determinants
       for (long long t = threadIdx.x; t < sh.gx_cnt; t += kRowThreads) {
         const uint32_t rk = A.grank[sh.gx_off + t];
-        atomicOr(&dy.touched[rk >> 5], 1u << (rk & 31));
+        atomicOr(&dy.touched[sector_word(rk)], sector_bit(rk));
       }
     }
     // candidates c = 0 .. ns+nd-1 (alpha singles then doubles of X); this CTA takes c = crank (mod gsz)
@@ -505,7 +511,13 @@ row_sweep_kernel(RowArgs A) {
         while (bits) {
           const int b = __ffs(bits) - 1;
           bits &= bits - 1u;
-          row[(size_t)w * 32 + b] = 0.0;
+          const int64_t e0 = ((int64_t)w * 32 + b) * 4;  // first entry of the sector
+          if (e0 + 3 < A.NB) {  // a whole sector: rows start on 32-byte boundaries
+            reinterpret_cast<double2*>(row + e0)[0] = make_double2(0.0, 0.0);
+            reinterpret_cast<double2*>(row + e0)[1] = make_double2(0.0, 0.0);
+          } else {
+            for (int64_t e = e0; e < A.NB; ++e) row[e] = 0.0;
+          }
         }
       }
     } else {  // clear this CTA's slice of the row
