@@ -89,9 +89,9 @@ struct RowDyn {
 
 __device__ __forceinline__ double fock_single(const RowArgs& A, const uint8_t* occ_all, int p, int q) {
   const int n = A.H.n;
-  double f = A.H.h[q * n + p];
+  double f = __ldg(&A.H.h[q * n + p]);
   const double* w = A.H.Ws + ((size_t)p * n + q) * n;
-  for (int t = 0; t < A.H.ne; ++t) f += w[occ_all[t]];
+  for (int t = 0; t < A.H.ne; ++t) f += __ldg(&w[occ_all[t]]);
   return f;
 }
 
@@ -129,7 +129,7 @@ __device__ __forceinline__ void row_pair(const RowArgs& A, double* row, unsigned
       atomicAdd(&row[rank_e], apply_sign(fock_single(A, occ_all, p, r), sb) * cd);
     } else {
       const int lo = p < r ? p : r, hi = p < r ? r : p;
-      const int k = A.H.ops1[lo * n + hi];
+      const int k = __ldg(&A.H.ops1[lo * n + hi]);
       if (A.sel_bits && !((__ldg(&A.sel_bits[k >> 5]) >> (k & 31)) & 1u)) return;
       const int sb = single_phase(d, p, r);
       atomicAdd(&A.g[k], apply_sign(cd * row[rank_e], sb ^ (int)(p > r)));
@@ -140,10 +140,10 @@ __device__ __forceinline__ void row_pair(const RowArgs& A, double* row, unsigned
   if (SCATTER) {
     if (!take(touched, filt, rank_e)) return;
     const int sb = double_phase(d, p, q, r, s);
-    atomicAdd(&row[rank_e], apply_sign(A.H.G[(size_t)pa * A.H.npairs + pb], sb) * cd);
+    atomicAdd(&row[rank_e], apply_sign(__ldg(&A.H.G[(size_t)pa * A.H.npairs + pb]), sb) * cd);
   } else {
     const bool down = pa > pb;
-    const int k = down ? A.H.opd[(size_t)pb * A.H.npairs + pa] : A.H.opd[(size_t)pa * A.H.npairs + pb];
+    const int k = __ldg(&A.H.opd[down ? (size_t)pb * A.H.npairs + pa : (size_t)pa * A.H.npairs + pb]);
     if (A.sel_bits && !((__ldg(&A.sel_bits[k >> 5]) >> (k & 31)) & 1u)) return;
     const int sb = double_phase(d, p, q, r, s);
     atomicAdd(&A.g[k], apply_sign(cd * row[rank_e], sb ^ (int)down));
@@ -231,8 +231,8 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
       for (int t2 = lane; t2 < A.H.ne; t2 += 32) {
         const int a = oa[t2];
         double jj = 0.0;
-        for (int u2 = 0; u2 < A.H.ne; ++u2) jj += A.H.J[a * A.H.n + oa[u2]];
-        hd += A.H.h[a * A.H.n + a] + 0.5 * jj;
+        for (int u2 = 0; u2 < A.H.ne; ++u2) jj += __ldg(&A.H.J[a * A.H.n + oa[u2]]);
+        hd += __ldg(&A.H.h[a * A.H.n + a]) + 0.5 * jj;
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) hd += __shfl_xor_sync(0xffffffffu, hd, o);
@@ -258,7 +258,7 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
         if (SCATTER) {
           if (take(touched, filt, re)) atomicAdd(&row[re], apply_sign(fock_single(A, oa, p, r), sb) * cd);
         } else {
-          const int k = A.H.ops1[(p < r ? p : r) * A.H.n + (p < r ? r : p)];
+          const int k = __ldg(&A.H.ops1[(p < r ? p : r) * A.H.n + (p < r ? r : p)]);
           if (!A.sel_bits || ((__ldg(&A.sel_bits[k >> 5]) >> (k & 31)) & 1u))
             atomicAdd(&A.g[k], apply_sign(cd * row[re], sb ^ (int)(p > r)));
         }
@@ -288,11 +288,11 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
         const int n = A.H.n;
         const double* w = A.H.Ws + ((size_t)pa * n + pb) * n;
         double f = 0.0;
-        for (int t3 = lane; t3 < A.H.ne; t3 += 32) f += w[oa[t3]];
+        for (int t3 = lane; t3 < A.H.ne; t3 += 32) f += __ldg(&w[oa[t3]]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
         if (lane == 0 && take(touched, filt, rd))
-          atomicAdd(&row[rd], apply_sign(A.H.h[pb * n + pa] + f, single_phase(d, pa, pb)) * cd);
+          atomicAdd(&row[rd], apply_sign(__ldg(&A.H.h[pb * n + pa]) + f, single_phase(d, pa, pb)) * cd);
       }
     } else if (lane == 0) {
       row_pair<SCATTER>(A, row, touched, filt, d, cd, A.grank[di], pa, -1, pb, -1, oa);
