@@ -221,8 +221,8 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
     const long long j = u / nch;
     const int ch = (int)(u - j * nch);
     const long long di = sh.gx_off + j;
-    const uint64_t d = A.gkey[di];
-    const double cd = A.gamp[di];
+    const uint64_t d = __ldg(&A.gkey[di]);
+    const double cd = __ldg(&A.gamp[di]);
     const uint32_t db = even_bits(d >> 1);
     warp_lists(sh, warp, lane, d, m);
     const uint8_t* oa = sh.occ_all[warp];
@@ -237,7 +237,7 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) hd += __shfl_xor_sync(0xffffffffu, hd, o);
       if (lane == 0) {
-        const uint32_t rd = A.grank[di];
+        const uint32_t rd = __ldg(&A.grank[di]);
         if (SCATTER) {
           if (take(touched, filt, rd)) atomicAdd(&row[rd], hd * cd);
         } else {
@@ -276,14 +276,14 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
     const int e = find_entry(dy.ents_s, sh.n_s, t);
     const RowEnt en = dy.ents_s[e];
     const long long di = (long long)en.off + (t - en.flat);
-    const uint64_t d = A.gkey[di];
-    const double cd = A.gamp[di];
+    const uint64_t d = __ldg(&A.gkey[di]);
+    const double cd = __ldg(&A.gamp[di]);
     const uint32_t db = even_bits(d >> 1);
     warp_lists(sh, warp, lane, d, m);
     const uint8_t* oa = sh.occ_all[warp];
     const int pa = en.o[0], pb = en.o[2];  // alpha spin-orbitals: removed, added
     if (SCATTER) {  // the alpha single itself: its Fock element summed across the warp
-      const uint32_t rd = A.grank[di];
+      const uint32_t rd = __ldg(&A.grank[di]);
       if (!filt || (touched[sector_word(rd)] & sector_bit(rd))) {  // the same word for every lane
         const int n = A.H.n;
         const double* w = A.H.Ws + ((size_t)pa * n + pb) * n;
@@ -295,7 +295,7 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
           atomicAdd(&row[rd], apply_sign(__ldg(&A.H.h[pb * n + pa]) + f, single_phase(d, pa, pb)) * cd);
       }
     } else if (lane == 0) {
-      row_pair<SCATTER>(A, row, touched, filt, d, cd, A.grank[di], pa, -1, pb, -1, oa);
+      row_pair<SCATTER>(A, row, touched, filt, d, cd, __ldg(&A.grank[di]), pa, -1, pb, -1, oa);
     }
     // alpha-beta doubles: phase = (beta single on D) ^ (alpha single on D) ^ (index-only bit in the tables)
     const int sa = single_phase(d, pa, pb);
@@ -365,8 +365,8 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
       while (e + 1 < sh.n_d && dy.ents_d[e + 1].flat <= t) ++e;
       const RowEnt en = dy.ents_d[e];
       const long long di = (long long)en.off + (t - en.flat);
-      row_pair<SCATTER>(A, row, touched, filt, A.gkey[di], A.gamp[di], A.grank[di], en.o[0], en.o[1], en.o[2], en.o[3],
-                        nullptr);
+      row_pair<SCATTER>(A, row, touched, filt, __ldg(&A.gkey[di]), __ldg(&A.gamp[di]), __ldg(&A.grank[di]), en.o[0],
+                        en.o[1], en.o[2], en.o[3], nullptr);
     }
   }
 }
@@ -422,7 +422,7 @@ row_sweep_kernel(RowArgs A) {
   // groups (the others hold no determinant whose sigma is read back)
   const int n_targets = A.energy_only ? (int)*A.n_groups : A.NA;
   for (int xi = cid; xi < n_targets; xi += ncl) {
-    const uint32_t X = A.energy_only ? even_bits(A.gkey[A.goff[xi]]) : A.alpha_list[xi];
+    const uint32_t X = A.energy_only ? even_bits(__ldg(&A.gkey[A.goff[xi]])) : A.alpha_list[xi];
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
       const bool inr = lane < m;
@@ -443,7 +443,7 @@ row_sweep_kernel(RowArgs A) {
     if (A.energy_only && sh.gx_cnt == 0) continue;  // same decision in every CTA of the cluster
     if (A.energy_only && dy.touched) {  // the entries that will be read back: X's own determinants
       for (long long t = threadIdx.x; t < sh.gx_cnt; t += kRowThreads) {
-        const uint32_t rk = A.grank[sh.gx_off + t];
+        const uint32_t rk = __ldg(&A.grank[sh.gx_off + t]);
         atomicOr(&dy.touched[sector_word(rk)], sector_bit(rk));
       }
     }
@@ -495,8 +495,8 @@ row_sweep_kernel(RowArgs A) {
     if (A.energy_only) {  // sigma_D of the determinants of X's own group
       for (long long t = (long long)crank * kRowThreads + threadIdx.x; t < sh.gx_cnt; t += (long long)gsz * kRowThreads) {
         const long long di = sh.gx_off + t;
-        const double sg = row[A.grank[di]];
-        e_acc += A.gamp[di] * sg;
+        const double sg = row[__ldg(&A.grank[di])];
+        e_acc += __ldg(&A.gamp[di]) * sg;
         if (A.sig_out) A.sig_out[A.gorig[di]] = sg;
       }
     } else {
