@@ -22,6 +22,9 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
                         two-level ground state of the first iteration, exact
                         one-parameter minimum of BFGS-2's first step, variational
                         bound and monotone energies against dense FCI
+  uccsd (MP2-ordered UCCSD guess, overlap and infidelity), in tests/test_uccsd_oracle.py:
+                        first-order coefficients and Koopmans orbital energies of the
+                        dense Hamiltonian, dense statevector overlaps
   spin (spin-complemented pool), in tests/test_spin_oracle.py: paired gradients
                         on flip-symmetrised states, commuting pairs against the
                         exponential of the summed generator
