@@ -98,6 +98,24 @@ int swcs_pool_ops(swcs_ctx* ctx, uint8_t* h_ops_out /* 5*pool_size bytes */);
  *   partner  [pool_size] host, int64;  sign  [pool_size] host, +1 or -1. */
 int swcs_pool_spin_pairs(swcs_ctx* ctx, int64_t* partner, int8_t* sign);
 
+/* MP2-ordered UCCSD ansatz (Sec. II.A, operators of Eqs. 2-3 relative to the
+ * reference): every S_z-conserving double i<j -> a<b (i, j occupied, a, b
+ * virtual; op bytes {2, i, j, a, b}) with its first-order amplitude as initial
+ * parameter, t = <ab||ij> / (e_i + e_j - e_a - e_b), e_p = h_pp + sum over the
+ * occupied k of <pk||pk>, largest |t| first (equal |t| keep the canonical
+ * (i, j, a, b) order); then every S_z-conserving single i -> a ({1, i, a, 0, 0})
+ * with parameter 0.  *n_out receives the operator count; h_ops [5*cap] and
+ * h_theta [cap] are written only when cap is large enough (pass NULL to size).
+ * Feed the result to swcs_apply_ansatz / swcs_energy_grad. */
+int swcs_mp2_uccsd(swcs_ctx* ctx, uint8_t* h_ops, double* h_theta, int64_t cap, int64_t* n_out);
+
+/* Overlap of the context's state with a sparse state given by the caller
+ * (distinct determinants, real amplitudes), for the infidelity against a
+ * reference wavefunction (Sec. IV.B): out4 = {<state|given>, <state|state>,
+ * <given|given>, 1 - <state|given>^2 / (<state|state> <given|given>)}.
+ * h_keys, h_amps [n] host; out4 [4] host.  Synchronises. */
+int swcs_overlap(swcs_ctx* ctx, const uint64_t* h_keys, const double* h_amps, int64_t n, double* out4);
+
 /* Evaluate the ansatz (Eq. 1) from |Psi_0>, truncating to n_keep after every
  * gate (n_keep <= 0: no truncation).  h_ops: 5*n_ops bytes; h_theta: n_ops.
  * The resulting state stays on the device in the context. */

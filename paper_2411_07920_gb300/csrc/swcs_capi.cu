@@ -54,6 +54,7 @@ struct swcs_ctx {
   DevBuf ctrl;  // n_state, tab_cur, err, bar, ctr, hist, stats, acc, eout
   DevBuf ops_dev, cs_dev;
   DevBuf gdev, subset_dev, gsub;
+  DevBuf ovl_keys, ovl_amps;  // swcs_overlap: the caller's state
 
   // row sweep: alpha strings of the sector, beta-rank tables, grouped state, rows
   DevBuf alpha_list, rank_tab, atab, gid_of, gcount, goff, gfill, gkey, gamp, grank, rows, rbeta, gab, kab, gorig;
@@ -113,6 +114,7 @@ struct Ctrl {
   double acc[2];
   double eout[2];
   unsigned long long n_distinct;
+  double ovl[3];  // swcs_overlap: <state|given>, <given|given>, <state|state>
 };
 
 int fail(swcs_ctx* c, int code, const char* fmt, ...) {
@@ -725,7 +727,8 @@ int swcs_destroy(swcs_ctx* c) {
   cudaStreamSynchronize(c->st);
   DevBuf* bufs[] = {&c->h, &c->J, &c->Ws, &c->G, &c->opd, &c->ops1, &c->gstage, &c->keys_a, &c->amps_a,
                     &c->keys_b, &c->amps_b, &c->tab0, &c->tab1, &c->ctrl, &c->ops_dev, &c->cs_dev,
-                    &c->gdev, &c->subset_dev, &c->gsub, &c->ext, &c->alpha_list, &c->rank_tab, &c->atab,
+                    &c->gdev, &c->subset_dev, &c->gsub, &c->ovl_keys, &c->ovl_amps, &c->ext, &c->alpha_list,
+                    &c->rank_tab, &c->atab,
                     &c->gid_of, &c->gcount, &c->goff, &c->gfill, &c->gkey, &c->gamp, &c->grank, &c->rows,
                     &c->rbeta, &c->gab, &c->kab, &c->gorig,
                     &c->ck_keys, &c->ck_amps, &c->ck_n, &c->sn_keys, &c->sn_amps, &c->sn_n, &c->sigma, &c->nu0,
@@ -911,6 +914,82 @@ int swcs_pool_spin_pairs(swcs_ctx* c, int64_t* partner, int8_t* sign) {
     partner[k] = it->second;
     sign[k] = (int8_t)sg;
   }
+  return SWCS_OK;
+}
+
+// MP2-ordered UCCSD ansatz (Sec. II.A): doubles i<j -> a<b of the reference with
+// their first-order amplitudes, largest |t| first (stable: equal |t| keep the
+// canonical order), then the singles at zero.
+int swcs_mp2_uccsd(swcs_ctx* c, uint8_t* h_ops, double* h_theta, int64_t cap, int64_t* n_out) {
+  int r = need_ham(c);
+  if (r) return r;
+  const int n = c->n, ne = c->ne;
+  std::vector<uint8_t> ijab;
+  for (int i = 0; i < ne; ++i)
+    for (int j = i + 1; j < ne; ++j)
+      for (int a = ne; a < n; ++a)
+        for (int b = a + 1; b < n; ++b)
+          if ((i & 1) + (j & 1) == (a & 1) + (b & 1))
+            ijab.insert(ijab.end(), {(uint8_t)i, (uint8_t)j, (uint8_t)a, (uint8_t)b});
+  std::vector<uint8_t> singles;
+  for (int i = 0; i < ne; ++i)
+    for (int a = ne; a < n; ++a)
+      if ((i & 1) == (a & 1)) singles.insert(singles.end(), {(uint8_t)i, (uint8_t)a});
+  const int64_t nd = (int64_t)ijab.size() / 4, ns = (int64_t)singles.size() / 2;
+  if (n_out) *n_out = nd + ns;
+  if (!h_ops || !h_theta || cap < nd + ns) return SWCS_OK;
+  std::vector<double> t(nd);
+  if (nd > 0) {
+    if ((r = ensure(c, c->gsub, ijab.size())) || (r = ensure(c, c->subset_dev, (size_t)nd * 8))) return r;
+    CK(cudaMemcpyAsync(c->gsub.p, ijab.data(), ijab.size(), cudaMemcpyHostToDevice, c->st));
+    CK(launch_k(c, kKOther, [&] {
+      return launch_mp2(ham_dev(c), (const uint8_t*)c->gsub.p, nd, (double*)c->subset_dev.p, c->st);
+    }));
+    CK(cudaMemcpyAsync(t.data(), c->subset_dev.p, (size_t)nd * 8, cudaMemcpyDeviceToHost, c->st));
+    if ((r = check_device(c, "swcs_mp2_uccsd"))) return r;
+  }
+  std::vector<int64_t> ord(nd);
+  for (int64_t q = 0; q < nd; ++q) ord[q] = q;
+  std::stable_sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return std::fabs(t[x]) > std::fabs(t[y]); });
+  for (int64_t q = 0; q < nd; ++q) {
+    const uint8_t* e = &ijab[4 * ord[q]];
+    uint8_t* o = h_ops + 5 * q;
+    o[0] = 2; o[1] = e[0]; o[2] = e[1]; o[3] = e[2]; o[4] = e[3];
+    h_theta[q] = t[ord[q]];
+  }
+  for (int64_t q = 0; q < ns; ++q) {
+    uint8_t* o = h_ops + 5 * (nd + q);
+    o[0] = 1; o[1] = singles[2 * q]; o[2] = singles[2 * q + 1]; o[3] = 0; o[4] = 0;
+    h_theta[nd + q] = 0.0;
+  }
+  return SWCS_OK;
+}
+
+// <state|given>, <state|state>, <given|given> and 1 - |<state|given>|^2 / (<state|state> <given|given>).
+int swcs_overlap(swcs_ctx* c, const uint64_t* h_keys, const double* h_amps, int64_t n, double* out4) {
+  int r = need_state(c);
+  if (r) return r;
+  if (!out4 || n < 0 || (n > 0 && (!h_keys || !h_amps))) return fail(c, SWCS_ERR_INVALID_ARG, "bad overlap arguments");
+  if ((r = ensure(c, c->ovl_keys, (size_t)std::max<int64_t>(n, 1) * 8)) ||
+      (r = ensure(c, c->ovl_amps, (size_t)std::max<int64_t>(n, 1) * 8)))
+    return r;
+  Ctrl* k = ctrl(c);
+  if (n > 0) {
+    CK(cudaMemcpyAsync(c->ovl_keys.p, h_keys, (size_t)n * 8, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->ovl_amps.p, h_amps, (size_t)n * 8, cudaMemcpyHostToDevice, c->st));
+  }
+  CK(cudaMemsetAsync(k->ovl, 0, 24, c->st));
+  CK(launch_k(c, kKOther, [&] {
+    return launch_overlap(state_dev(c), (const uint64_t*)c->ovl_keys.p, (const double*)c->ovl_amps.p, n, k->ovl,
+                          c->nsm * 4, c->st);
+  }));
+  double v[3];
+  CK(cudaMemcpyAsync(v, k->ovl, 24, cudaMemcpyDeviceToHost, c->st));
+  if ((r = check_device(c, "swcs_overlap"))) return r;
+  out4[0] = v[0];
+  out4[1] = v[2];
+  out4[2] = v[1];
+  out4[3] = (v[1] > 0.0 && v[2] > 0.0) ? 1.0 - v[0] * v[0] / (v[2] * v[1]) : 1.0;
   return SWCS_OK;
 }
 

@@ -226,6 +226,10 @@ cudaError_t launch_mlp_gemm(const GemmArgs& g, cudaStream_t st);
 // layer-by-layer kernel sums the same way, so both round identically.
 constexpr int kDotGroups = 4;
 __host__ __device__ __forceinline__ int dot_group_begin(int g, int nchunks) { return g * nchunks / kDotGroups; }
+// UCCSD guess and overlap (swcs_guess.cu).
+cudaError_t launch_mp2(const HamDev& H, const uint8_t* ijab, int64_t nd, double* t, cudaStream_t st);
+cudaError_t launch_overlap(const StateDev& S, const uint64_t* keys, const double* amps, int64_t n, double* out,
+                           int nblocks, cudaStream_t st);
 // Fused inference forward (all three layers in one persistent tcgen05 kernel).
 struct FusedArgs {
   int64_t M;                // rows (pool operators)

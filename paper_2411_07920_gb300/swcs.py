@@ -41,6 +41,8 @@ _SIGS = {
     "swcs_pool_size": ([_vp, _p64], _i),
     "swcs_pool_ops": ([_vp, _vp], _i),
     "swcs_pool_spin_pairs": ([_vp, _vp, _vp], _i),
+    "swcs_mp2_uccsd": ([_vp, _vp, _vp, _i64, _p64], _i),
+    "swcs_overlap": ([_vp, _vp, _vp, _i64, _vp], _i),
     "swcs_apply_ansatz": ([_vp, _vp, _vp, _i, _i64], _i),
     "swcs_apply_ansatz_dev": ([_vp, _vp, _vp, _i, _i64], _i),
     "swcs_apply_gates": ([_vp, _vp, _vp, _i, _i64], _i),
@@ -325,6 +327,23 @@ class Context:
         out = np.zeros(5 * self.pool_size(), np.uint8)
         self._ck(lib.swcs_pool_ops(self._h, _ptr(out)))
         return out.reshape(-1, 5)
+
+    def mp2_uccsd(self):
+        """(ops [M, 5] uint8, theta [M]) of the MP2-ordered UCCSD ansatz."""
+        n = ctypes.c_int64()
+        self._ck(lib.swcs_mp2_uccsd(self._h, None, None, 0, ctypes.byref(n)))
+        ops = np.zeros(5 * n.value, np.uint8)
+        theta = np.zeros(n.value)
+        self._ck(lib.swcs_mp2_uccsd(self._h, _ptr(ops), _ptr(theta), n.value, ctypes.byref(n)))
+        return ops.reshape(-1, 5), theta
+
+    def overlap(self, keys, amps):
+        """(<state|given>, <state|state>, <given|given>, infidelity)."""
+        keys = _c(keys, np.uint64)
+        amps = _c(amps, np.float64)
+        out = np.zeros(4)
+        self._ck(lib.swcs_overlap(self._h, _ptr(keys), _ptr(amps), len(keys), _ptr(out)))
+        return tuple(float(x) for x in out)
 
     def pool_spin_pairs(self):
         """(partner, sign): the spin flip of kappa_k is sign[k] * kappa_partner[k]."""
