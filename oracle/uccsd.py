@@ -72,3 +72,14 @@ def infidelity(keys_a, amps_a, keys_b, amps_b):
     aa = float(np.dot(amps_a, amps_a))
     bb = float(np.dot(amps_b, amps_b))
     return 1.0 - ab * ab / (aa * bb)
+
+
+def vqe(n_so, n_e, h, g, ops, theta0, n_keep, gtol=1e-6):
+    """BFGS (SciPy, Sec. III) over the oracle's energy and adjoint gradient for
+    a fixed ansatz; returns (E, theta)."""
+    import scipy.optimize as so
+    from . import oracle as O
+    res = so.minimize(lambda x: O.energy_grad(n_so, n_e, h, g, ops, x, n_keep), np.asarray(theta0, np.float64),
+                      jac=True, method="BFGS", options={"gtol": gtol})
+    keys, amps = O.apply_ansatz(n_so, n_e, ops, res.x, n_keep)
+    return O.energy(n_so, h, g, keys, amps)[0], np.asarray(res.x, np.float64)

@@ -204,3 +204,17 @@ def bootstrap(ctx, schedule, max_iter, eps=1e-2, gtol=1e-6, first="bfgs2", then=
         stages.append(dict(n_keep=int(n_keep), n_params=len(a.theta), converged=conv,
                            stalled=bool(a.history and a.history[-1].stalled), energy=a.history[-1].energy))
     return a, stages
+
+
+def vqe(ctx, ops, theta0, n_keep, gtol=1e-6, ckpt_every=20):
+    """VQE for a fixed ansatz (Eq. 1), e.g. the MP2-ordered UCCSD of
+    ctx.mp2_uccsd(): SciPy BFGS over swcs_energy_grad.  Returns (E, theta, calls)."""
+    calls = [0]
+
+    def fun(x):
+        calls[0] += 1
+        return ctx.energy_grad(ops, x, n_keep, ckpt_every)
+    res = opt.minimize(fun, np.asarray(theta0, np.float64), jac=True, method="BFGS", options={"gtol": gtol})
+    theta = np.asarray(res.x, np.float64)
+    ctx.apply_ansatz(ops, theta, n_keep)
+    return ctx.energy()[0], theta, calls[0]

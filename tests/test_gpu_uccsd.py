@@ -48,3 +48,16 @@ def test_overlap_and_infidelity_match_oracle(S, n_so, n_e, n_keep):
     assert abs(inf - infidelity(ka, aa, kb, ab)) < 1e-12
     assert abs(c.overlap(ka, aa)[3]) < 1e-13                      # with itself
     assert c.overlap(np.zeros(0, np.uint64), np.zeros(0))[0] == 0.0  # empty given state
+
+
+def test_uccsd_vqe_matches_oracle(S):
+    from oracle.uccsd import vqe as oracle_vqe
+    from paper_2411_07920_gb300 import adapt
+    w = I.workload("so12_e4")
+    c = S.Context()
+    c.load_hamiltonian(w.h, w.g, w.n_so, w.n_e)
+    ops, theta = c.mp2_uccsd()
+    e, th, calls = adapt.vqe(c, ops, theta, 0)
+    eo, tho = oracle_vqe(w.n_so, w.n_e, w.h, w.g, ops, theta, 0)
+    assert calls > 1
+    assert abs(e - eo) < 1e-9

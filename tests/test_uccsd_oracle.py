@@ -89,3 +89,21 @@ def test_overlap_and_infidelity_against_dense_vectors():
     assert abs(infidelity(k, a, kf, af) - ref) < 1e-13
     assert abs(infidelity(k, a, k, 3.0 * a)) < 1e-15
     assert infidelity(k[:1], a[:1], k[1:2], a[1:2]) == 1.0
+
+
+def test_uccsd_vqe_is_bounded_by_fci_and_the_reference():
+    w = I.workload("so12_e4")
+    n, ne = w.n_so, w.n_e
+    from oracle.uccsd import vqe
+    ops, theta = mp2_uccsd(w.h, w.g, n, ne)
+    e, th = vqe(n, ne, w.h, w.g, ops, theta, 0)
+    basis = J.sector(n, ne)
+    H = J.hamiltonian_sector(n, w.h, w.g, basis)
+    efci = np.linalg.eigvalsh(H)[0]
+    hf = (1 << ne) - 1
+    e_hf = H[int(np.flatnonzero(basis == hf)[0]), int(np.flatnonzero(basis == hf)[0])]
+    k, a = O.apply_ansatz(n, ne, ops, theta, 0)
+    e_mp2 = O.energy(n, w.h, w.g, k, a)[0]
+    assert efci - 1e-12 <= e <= e_mp2 + 1e-12 and e < e_hf
+    _, d = O.energy_grad(n, ne, w.h, w.g, ops, th, 0)
+    assert np.abs(d).max() < 1e-5
