@@ -490,6 +490,9 @@ row_sweep_kernel(RowArgs A) {
     scan_items<kRowThreads>(sh, dy.ents_s, sh.n_s, 1, &sh.tot_s);
     scan_items<kRowThreads>(sh, dy.ents_d, sh.n_d, kDblChunk, &sh.tot_d);
 
+    // the other CTA may still be clearing the previous target's sectors: wait for it before scattering
+    // (the clear itself flows straight into this target's discovery)
+    cl.sync();
     row_phase<kRowThreads, true>(A, sh, dy, row, crank, gsz, e_acc);
     cl.sync();
     if (A.energy_only) {  // sigma_D of the determinants of X's own group
@@ -525,7 +528,6 @@ row_sweep_kernel(RowArgs A) {
       const int64_t b = per * crank, e = (A.NB < b + per) ? A.NB : b + per;
       for (int64_t i = b + threadIdx.x; i < e; i += kRowThreads) row[i] = 0.0;
     }
-    cl.sync();
   }
   // energy numerator
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
