@@ -272,8 +272,9 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
     __syncwarp();
   }
   // ---------------- alpha-single neighbours: alpha single + alpha-beta doubles (warp per determinant)
+  int e = 0;  // a warp's items only increase: walk its entry forward instead of searching
   for (uint32_t t = warp; t < sh.tot_s; t += kRowWarps) {
-    const int e = find_entry(dy.ents_s, sh.n_s, t);
+    while (e + 1 < sh.n_s && dy.ents_s[e + 1].flat <= t) ++e;
     const RowEnt en = dy.ents_s[e];
     const long long di = (long long)en.off + (t - en.flat);
     const uint64_t d = __ldg(&A.gkey[di]);
