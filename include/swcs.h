@@ -260,7 +260,8 @@ int swcs_profile_read(swcs_ctx* ctx, double* h_ms8, int64_t* h_launches8, int re
  *   swcs_mlp_activations: H1, H2 (BF16 bits) and y of the last grad/train call.
  *   swcs_pool_features_dev: SWCS_MLP_FEATURES features of every pool operator
  *   for the context's current state, BF16 bits [pool_size][32].
- *   swcs_pool_screen_dev: features, network, and the indices of the
+ *   swcs_pool_screen_dev: features, network (the fused inference kernel of
+ *   swcs_mlp_predict_dev), and the indices of the
  *   ceil(frac * pool_size) largest predictions into d_subset (device,
  *   pool_size capacity, unordered); *h_n_subset receives the count.
  *   Feed them to swcs_pool_gradients_dev to evaluate only those operators.
