@@ -10,14 +10,17 @@
 // alpha-beta double) or one alpha double away (alpha-alpha double).  For a
 // fixed X all sigma_E therefore live in one dense row indexed by the
 // combinatorial rank of E_beta (C(n/2, n_e/2) doubles, 1.84 MB at 52/12),
-// which a thread-block cluster keeps in L2:
+// owned by one thread-block cluster while it works on X:
 //   1. the cluster finds the alpha groups of S at distance 0, 1, 2 from X
 //      (alpha-string hash table of S);
-//   2. scatter: every pair adds <E|H|D> c_D into row[rank(E_beta)];
+//   2. scatter: every pair adds <E|H|D> c_D into row[rank(E_beta)], marking
+//      the 32-byte sector it touched;
 //   3. cluster barrier; gather: every pair adds dir*phase*c_D*row[...] to
 //      g_k, and the diagonal pairs give the energy numerator;
-//   4. cluster barrier; the cluster clears the row; barrier; next X.
-// No hashing or compare-and-swap on sigma, and no sigma traffic to HBM.
+//   4. cluster barrier; each CTA zeroes the sectors it touched, finds the
+//      next X's neighbours, and waits at the barrier before its scatter.
+// No hashing or compare-and-swap on sigma.  The rows of all clusters share L2;
+// when they exceed it (228 rows at 52/12) their sectors spill to HBM.
 #include <cooperative_groups.h>
 #include <cstdint>
 #include <cuda_runtime.h>
