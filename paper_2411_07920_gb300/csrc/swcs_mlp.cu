@@ -2,8 +2,11 @@
 // predicts log10|g_k| of every pool operator from per-operator features, so
 // that only the predicted top fraction of the pool is evaluated exactly.
 //
-// All dense contractions run on the 5th-generation tensor cores through one
-// kernel, C[M x N] = A[M x K] . B[N x K]^T with A, B BF16 and K contiguous:
+// Training and the layer-by-layer forward (which keeps the activations for the
+// backward pass) run their dense contractions on the 5th-generation tensor
+// cores through one kernel, C[M x N] = A[M x K] . B[N x K]^T with A, B BF16
+// and K contiguous (inference over the pool uses the fused kernel of
+// swcs_mlp_fused.cu instead):
 //   - a CTA of 128 threads owns a 128-row tile and all N <= 256 columns;
 //   - K is consumed in chunks of 32: the CTA copies the A and B chunks into
 //     shared memory in the canonical no-swizzle K-major layout (8x16-byte core
