@@ -547,8 +547,10 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
   ga.acc = k->acc;
   CK(launch_k(c, kKGroup, [&] { return launch_group_state(ga, c->st); }));
   c->launches += 4;  // five grouping kernels in one call
+  // beta-single entries carry the spatial pair i * m + j too when ranks fit 21 bits and pairs 10
+  const int rbeta_packed = c->NB <= (1 << 21) && m <= 32 ? 1 : 0;
   CK(launch_k(c, kKGroup, [&] {
-    return launch_rbeta(ga.gkey, ga.n, ga.rank_tab, ks, nvs, m, (uint32_t*)c->rbeta.p, c->st);
+    return launch_rbeta(ga.gkey, ga.n, ga.rank_tab, ks, nvs, m, rbeta_packed, (uint32_t*)c->rbeta.p, c->st);
   }));
   RowArgs ra;
   ra.H = ham_dev(c);
@@ -571,6 +573,7 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
   ra.touched_words = twords;
   ra.sel_bits = sel;
   ra.rbeta = (const uint32_t*)c->rbeta.p;
+  ra.rbeta_packed = rbeta_packed;
   ra.gab = (const double*)c->gab.p;
   ra.kab = (const int*)c->kab.p;
   ra.energy_only = energy_only ? 1 : 0;

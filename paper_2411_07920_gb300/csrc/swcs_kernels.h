@@ -128,6 +128,7 @@ struct RowArgs {
   // beta single excitations of each grouped determinant, t = occ_slot*nv + vir_slot:
   // rank of the new beta string | (phase bit << 31)
   const uint32_t* rbeta;
+  int rbeta_packed;  // entries also carry the spatial pair i * m + j in bits 21..30 (NB <= 2^21)
   // alpha-beta doubles by spatial indices (a -> b alpha, i -> j beta), [m^4]:
   // integral with the index-only part of the phase folded in, and the pool
   // index | (direction and index-only phase bit << 31)
@@ -167,7 +168,7 @@ cudaError_t launch_row_sweep(const RowArgs& a, int threads, int occ, int gsz, in
                              cudaStream_t st);
 cudaError_t launch_group_state(const GroupArgs& g, cudaStream_t st);
 cudaError_t launch_rbeta(const uint64_t* gkey, const long long* n, const uint32_t* rank_tab, int ks, int nv, int m,
-                         uint32_t* rbeta, cudaStream_t st);
+                         int packed, uint32_t* rbeta, cudaStream_t st);
 
 // Adjoint (swcs_adjoint.cu).
 cudaError_t launch_build_index(const uint64_t* keys, const long long* n, IdxSlot* tab, uint64_t mask, cudaStream_t st);

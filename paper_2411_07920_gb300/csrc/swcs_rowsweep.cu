@@ -217,6 +217,10 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
   const int t_same = 1 + ks * nvs + (ks * (ks - 1) / 2) * n_tv;
   const int nch = (t_same + kSameChunk - 1) / kSameChunk;
   unsigned* touched = SCATTER ? dy.touched : nullptr;
+  // beta-single table entries: rank | phase << 31, and when packed also the (occupied, virtual) spatial
+  // pair i * m + j in bits 21..30 (rows of at most 2^21 entries)
+  const bool packed = A.rbeta_packed != 0;
+  const uint32_t rmask = packed ? 0x1FFFFFu : 0x7FFFFFFFu;
   const bool filt = SCATTER && A.energy_only && dy.touched != nullptr;
   // ---------------- X's own group: diagonal, beta singles, beta-beta doubles; items (determinant, chunk)
   const long long n_items_same = sh.gx_cnt * nch;
@@ -255,7 +259,7 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
       if (o2 == 255) {  // beta single: rank and phase precomputed for this determinant
         const int i = sh.bocc[warp][o1], jv = sh.bvir[warp][v1];
         const uint32_t wb = __ldg(&A.rbeta[(size_t)di * (ks * nvs) + o1 * nvs + v1]);
-        const uint32_t re = wb & 0x7FFFFFFFu;
+        const uint32_t re = wb & rmask;
         const int sb = (int)(wb >> 31);
         const int p = 2 * i + 1, r = 2 * jv + 1;
         if (SCATTER) {
@@ -310,17 +314,17 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
       if (filt) {  // energy only: almost every target is skipped, so test before loading the integral
         for (int t2 = lane; t2 < nsb; t2 += 32) {
           const uint32_t wb = __ldg(&rb[t2]);
-          const uint32_t re = wb & 0x7FFFFFFFu;
+          const uint32_t re = wb & rmask;
           if (!take(touched, true, re)) continue;
-          const int i = sh.bocc[warp][t2 / nvs], j = sh.bvir[warp][t2 % nvs];
-          atomicAdd(&row[re], apply_sign(__ldg(&A.gab[base + (size_t)i * m + j]), (int)(wb >> 31) ^ sa) * cd);
+          const uint32_t ij = packed ? (wb >> 21) & 1023u : (uint32_t)(sh.bocc[warp][t2 / nvs] * m + sh.bvir[warp][t2 % nvs]);
+          atomicAdd(&row[re], apply_sign(__ldg(&A.gab[base + ij]), (int)(wb >> 31) ^ sa) * cd);
         }
       } else {  // both loads issued up front, off the atomic's dependency chain
         for (int t2 = lane; t2 < nsb; t2 += 32) {
-          const int i = sh.bocc[warp][t2 / nvs], j = sh.bvir[warp][t2 % nvs];
           const uint32_t wb = __ldg(&rb[t2]);
-          const double gv = __ldg(&A.gab[base + (size_t)i * m + j]);
-          const uint32_t re = wb & 0x7FFFFFFFu;
+          const uint32_t ij = packed ? (wb >> 21) & 1023u : (uint32_t)(sh.bocc[warp][t2 / nvs] * m + sh.bvir[warp][t2 % nvs]);
+          const double gv = __ldg(&A.gab[base + ij]);
+          const uint32_t re = wb & rmask;
           take(touched, false, re);
           atomicAdd(&row[re], apply_sign(gv, (int)(wb >> 31) ^ sa) * cd);
         }
@@ -340,11 +344,11 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
           kk[u] = 0;
           sb[u] = 0;
           if (ok[u]) {
-            const int i = sh.bocc[warp][t2 / nvs], j = sh.bvir[warp][t2 % nvs];
             const uint32_t wb = __ldg(&rb[t2]);
-            re[u] = wb & 0x7FFFFFFFu;
+            const uint32_t ij = packed ? (wb >> 21) & 1023u : (uint32_t)(sh.bocc[warp][t2 / nvs] * m + sh.bvir[warp][t2 % nvs]);
+            re[u] = wb & rmask;
             sb[u] = (int)(wb >> 31) ^ sa;
-            kk[u] = __ldg(&A.kab[base + (size_t)i * m + j]);
+            kk[u] = __ldg(&A.kab[base + ij]);
             const int k = kk[u] & 0x7FFFFFFF;
             if (A.sel_bits && !((__ldg(&A.sel_bits[k >> 5]) >> (k & 31)) & 1u)) ok[u] = false;
           }
@@ -628,7 +632,7 @@ __global__ void group_scatter_kernel(const uint64_t* keys, const double* amps, c
 // Beta single excitations of every grouped determinant: rank of the new beta
 // string and the phase bit of a+_{2j+1} a_{2i+1} on D, t = occ_slot*nv + vir_slot.
 __global__ void rbeta_kernel(const uint64_t* gkey, const long long* n_ptr, const uint32_t* rank_tab, int ks, int nv,
-                             int m, uint32_t* rbeta) {
+                             int m, int packed, uint32_t* rbeta) {
   const long long n = *n_ptr;
   const int lane = threadIdx.x & 31;
   const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -647,7 +651,8 @@ __global__ void rbeta_kernel(const uint64_t* gkey, const long long* n_ptr, const
       const int j = __ffs(y) - 1;
       const uint32_t re = str_rank(rank_tab, ks, db ^ (1u << i) ^ (1u << j));
       const int sb = single_phase(d, 2 * i + 1, 2 * j + 1);
-      rbeta[(size_t)di * (ks * nv) + t] = re | ((uint32_t)sb << 31);
+      const uint32_t ij = packed ? ((uint32_t)(i * m + j) << 21) : 0u;
+      rbeta[(size_t)di * (ks * nv) + t] = re | ij | ((uint32_t)sb << 31);
     }
   }
 }
@@ -655,8 +660,8 @@ __global__ void rbeta_kernel(const uint64_t* gkey, const long long* n_ptr, const
 }  // namespace
 
 cudaError_t launch_rbeta(const uint64_t* gkey, const long long* n, const uint32_t* rank_tab, int ks, int nv, int m,
-                         uint32_t* rbeta, cudaStream_t st) {
-  rbeta_kernel<<<1216, 256, 0, st>>>(gkey, n, rank_tab, ks, nv, m, rbeta);
+                         int packed, uint32_t* rbeta, cudaStream_t st) {
+  rbeta_kernel<<<1216, 256, 0, st>>>(gkey, n, rank_tab, ks, nv, m, packed, rbeta);
   return cudaGetLastError();
 }
 

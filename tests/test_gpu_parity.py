@@ -262,6 +262,35 @@ def test_largest_orbital_space(S, n_e, n_keep, sweep):
     assert np.abs(g - go).max() < TOL
 
 
+def test_rows_above_two_million_entries(S):
+    """64 spin-orbitals and 14 electrons: beta strings of 7 electrons in 32 orbitals give rows of
+    3,365,856 entries, above the 2^21 ranks that the packed beta-single entries hold, so the row sweep
+    looks the beta pair up from the strings' orbital lists instead."""
+    n_e, n_keep = 14, 120
+    assert math.comb(32, 7) > 1 << 21
+    w = I.small_case(64, n_e, 24, 140 + n_e, n_keep=n_keep)
+    top = np.array([[2, 0, 1, 62, 63], [1, n_e - 1, 63, 0, 0]], np.uint8)
+    ops = np.concatenate([w.ops, top])
+    theta = np.concatenate([w.theta, [0.4, -0.3]])
+    c = ctx_for(S, w)
+    c.apply_ansatz(ops, theta, n_keep)
+    k, a = c.get_state()
+    ko, ao = O.apply_ansatz(64, n_e, ops, theta, n_keep)
+    assert_state_equal(k, a, ko, ao)
+    e, _ = c.energy()
+    assert abs(e - O.energy(64, w.h, w.g, ko, ao)[0]) < TOL
+    c.set_option("sweep", 2)
+    g = c.pool_gradients()
+    assert len(g) == 708784
+    rng = np.random.default_rng(1)
+    sub = np.sort(rng.choice(len(g), 300, replace=False)).astype(np.int64)
+    go = O.pool_gradients(64, w.h, w.g, ko, ao, subset=sub)
+    assert np.abs(g[sub] - go[sub]).max() < TOL
+    assert abs(c.sweep_energy()[0] - e) < TOL
+    c.set_option("sweep", 1)
+    assert np.abs(c.pool_gradients() - g).max() < TOL
+
+
 @pytest.mark.parametrize("n_so,n_e", [(12, 2), (12, 10), (8, 6), (4, 2)])
 def test_nearly_empty_and_nearly_full_sectors(S, n_so, n_e):
     """One electron or one hole per spin: no same-spin doubles on one side, so the row sweep's
