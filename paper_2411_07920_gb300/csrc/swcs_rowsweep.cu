@@ -167,6 +167,15 @@ __device__ __forceinline__ void warp_lists(RowShared& sh, int warp, int lane, ui
   __syncwarp();
 }
 
+// The occupied spin-orbitals of d only (what the Fock element of a single needs).
+__device__ __forceinline__ void warp_occ(RowShared& sh, int warp, int lane, uint64_t d) {
+  const unsigned below = (1u << lane) - 1u;
+  const unsigned lo = (unsigned)d, hi = (unsigned)(d >> 32);
+  if ((lo >> lane) & 1u) sh.occ_all[warp][__popc(lo & below)] = (uint8_t)lane;
+  if ((hi >> lane) & 1u) sh.occ_all[warp][__popc(lo) + __popc(hi & below)] = (uint8_t)(32 + lane);
+  __syncwarp();
+}
+
 // Block-wide exclusive scan, in list order, of the work items of each entry:
 // ceil(group size / chunk).
 template <int kRowThreads>
@@ -286,8 +295,9 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
     const long long di = (long long)en.off + (t - en.flat);
     const uint64_t d = __ldg(&A.gkey[di]);
     const double cd = __ldg(&A.gamp[di]);
-    const uint32_t db = even_bits(d >> 1);
-    warp_lists(sh, warp, lane, d, m);
+    // packed beta-single entries need no beta lists; the gather needs no occupied list either
+    if (!packed) warp_lists(sh, warp, lane, d, m);
+    else if (SCATTER) warp_occ(sh, warp, lane, d);
     const uint8_t* oa = sh.occ_all[warp];
     const int pa = en.o[0], pb = en.o[2];  // alpha spin-orbitals: removed, added
     if (SCATTER) {  // the alpha single itself: its Fock element summed across the warp
