@@ -120,3 +120,20 @@ def test_host_bootstrap_matches_the_oracle_bootstrap(adapt):
         assert [s[key] for s in st] == [s[key] for s in st_ref]
     assert a.chosen == ref.chosen
     assert np.abs(np.array(_accepted(a)) - np.array(ref.energies)).max() < 1e-12
+
+
+def test_autograd_wrapper_carries_the_adjoint():
+    """SwcsEnergy (paper_2411_07920_gb300.autograd) returns E and hands the
+    stored dE/dtheta to torch's backward, scaled by the incoming gradient."""
+    import torch
+    from paper_2411_07920_gb300.autograd import energy
+    w = I.small_case(12, 4, 6, 1)
+    ctx = OracleContext(w)
+    e_ref, d_ref = O.energy_grad(w.n_so, w.n_e, w.h, w.g, w.ops, w.theta, 0)
+    theta = torch.tensor(w.theta, dtype=torch.float64, requires_grad=True)
+    e = energy(theta, ctx, w.ops, 0)
+    assert abs(e.item() - e_ref) < 1e-14
+    (g,) = torch.autograd.grad(3.0 * e, theta)
+    assert np.abs(g.numpy() - 3.0 * d_ref).max() < 1e-14
+    # untruncated, the adjoint is the derivative of the forward: torch's finite-difference check
+    assert torch.autograd.gradcheck(lambda t: energy(t, ctx, w.ops, 0), (theta,), eps=1e-6, atol=1e-7)
