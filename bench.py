@@ -37,7 +37,7 @@ WORKLOAD = "so52_e12"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=5)
@@ -59,7 +59,7 @@ def parse():
     p.add_argument("--no-adapt", action="store_true", help="skip the ADAPT-VQE leg")
     p.add_argument("--adapt-n-keep", type=int, default=10_000, help="N_CUT of the ADAPT-VQE leg")
     p.add_argument("--adapt-iters", type=int, default=30, help="ADAPT iterations of the ADAPT-VQE leg")
-    return p.parse_args()
+    return p.parse_args(argv)
 
 
 def dist_env():
@@ -277,7 +277,7 @@ def run_swcs(args):
         bytes_per_launch = 16.0 * pairs
     achieved = bytes_per_launch / (dom_ms / dom_n / 1e3) / 1e9
     roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": achieved / hbm_peak, "traffic": measured_traffic(dom),
+            "frac": achieved / hbm_peak, "traffic": measured_traffic(dom, args),
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     gate_ms = prof.get("ansatz", (0.0, 0))[0]
     gate_dets_per_s = stats["gate_dets"] / (gate_ms / 1e3) if gate_ms > 0 else None
@@ -374,12 +374,19 @@ def aggregate(total_ms, steps, world, device):
     return total_ms / steps, world * steps / (total_ms / 1e3)
 
 
-def measured_traffic(kernel):
+# the launch the committed row-sweep traffic was captured on: the default workload and launch shape
+TRAFFIC_CAPTURED = dict(n_keep=1_000_000, cluster=2, rows_l2=0, threads=512, row_clusters=0, row_occupancy=3)
+
+
+def measured_traffic(kernel, args):
     """DRAM bytes per launch of the dominant kernel from its committed ncu summary,
-    only while the kernel's source is the one that was captured (else None)."""
+    only for the workload and launch shape that were captured and while the
+    kernel's source is the one that was captured (else None)."""
     import hashlib
     files = {"row_sweep": ("profiles/row_sweep_so52_e12_N1e6.md", "paper_2411_07920_gb300/csrc/swcs_rowsweep.cu")}
     if kernel not in files:
+        return None
+    if args.sweep == 1 or any(getattr(args, k) != v for k, v in TRAFFIC_CAPTURED.items()):
         return None
     summary, src = (os.path.join(ROOT, f) for f in files[kernel])
     try:

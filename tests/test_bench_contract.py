@@ -24,3 +24,17 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in d["config"]
+
+
+def test_committed_traffic_is_reported_only_for_the_captured_launch():
+    """The ncu DRAM traffic in the row-sweep summary belongs to the default
+    workload and launch shape; any other bench configuration reports null."""
+    sys.path.insert(0, ROOT)
+    import bench
+    text = open(os.path.join(ROOT, "profiles", "row_sweep_so52_e12_N1e6.md")).read()
+    committed = int(text.split("traffic_bytes_per_launch:")[1].split()[0])
+    assert bench.measured_traffic("row_sweep", bench.parse([])) in (committed, None)
+    for argv in (["--n-keep", "300000"], ["--threads", "256"], ["--cluster", "1"], ["--row-occupancy", "2"],
+                 ["--rows-l2", "1"], ["--sweep", "1"]):
+        assert bench.measured_traffic("row_sweep", bench.parse(argv)) is None, argv
+    assert bench.measured_traffic("ansatz", bench.parse([])) is None
