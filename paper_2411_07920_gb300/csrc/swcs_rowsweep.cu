@@ -206,14 +206,22 @@ __device__ void scan_items(RowShared& sh, RowEnt* ents, int cnt, int chunk, uint
   __syncthreads();
 }
 
-__device__ __forceinline__ int find_entry(const RowEnt* ents, int cnt, uint32_t t) {
-  int lo = 0, hi = cnt - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (ents[mid].flat <= t) lo = mid;
-    else hi = mid - 1;
+// The last entry whose first work item is at or before item t (entries in
+// list order, prefixes increasing), found by the whole warp: 32-ary search
+// steps, one ballot each; every lane of the warp must call it.  ents[lo].flat
+// <= t holds throughout (ents[0].flat = 0), so lane 0's probe is always true
+// and the ballot never empty.
+__device__ __forceinline__ int warp_find_entry(const RowEnt* ents, int cnt, uint32_t t, int lane) {
+  int lo = 0, span = cnt;  // the entry lies in [lo, lo + span)
+  while (span > 32) {
+    const int stride = (span + 31) >> 5;
+    const bool le = lane * stride < span && ents[lo + lane * stride].flat <= t;
+    const int k = 31 - __clz(__ballot_sync(0xffffffffu, le));
+    lo += k * stride;
+    span = min(stride, span - k * stride);
   }
-  return lo;
+  const bool le = lane < span && ents[lo + lane].flat <= t;
+  return lo + 31 - __clz(__ballot_sync(0xffffffffu, le));
 }
 
 template <int kRowThreads, bool SCATTER>
@@ -372,12 +380,16 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
     }
     __syncwarp();
   }
-  // ---------------- alpha-double neighbours: one determinant per lane; lane 0 of each warp
-  // finds the entry of the warp's first item, the other lanes walk forward from it
+  // ---------------- alpha-double neighbours: one determinant per lane; the warp finds the entry of
+  // its first item, then each lane counts the entries that start at or before its own item (lane j
+  // marks where entry e + j starts inside the warp's 32 items: groups hold at least one determinant,
+  // so the starts are distinct and the walk below takes no step)
   for (uint32_t t0 = (uint32_t)warp * 32; t0 < sh.tot_d; t0 += kRowThreads) {
-    int e = 0;
-    if (lane == 0) e = find_entry(dy.ents_d, sh.n_d, t0);
-    e = __shfl_sync(0xffffffffu, e, 0);
+    int e = warp_find_entry(dy.ents_d, sh.n_d, t0, lane);
+    const int ej = e + lane;
+    const uint32_t st = (lane > 0 && ej < sh.n_d) ? dy.ents_d[ej].flat - t0 : 32u;
+    const unsigned starts = __reduce_or_sync(0xffffffffu, st < 32u ? 1u << st : 0u);
+    e += __popc(starts & ((2u << lane) - 1u));
     const uint32_t t = t0 + lane;
     if (t < sh.tot_d) {
       while (e + 1 < sh.n_d && dy.ents_d[e + 1].flat <= t) ++e;
