@@ -220,15 +220,19 @@ int swcs_set_option(swcs_ctx* ctx, const char* name, int64_t value);
  *   d_keys, d_amps  [n] device arrays: distinct determinants of the loaded
  *                   Hamiltonian's sector and their amplitudes (no zeros needed)
  *   n               1 <= n <= SWCS_NOALLOC_MAX_DETS, else SWCS_ERR_INVALID_ARG
- *   d_out           [2] device: E and <psi|psi>
+ *   d_out           [2] device: E and <psi|psi>; both NaN when a determinant
+ *                   appears twice or lies outside the sector (bits >= n_so,
+ *                   wrong electron count, S_z != 0): the check runs on the
+ *                   device, so the call itself still returns SWCS_OK
  * Needs a loaded Hamiltonian (swcs_load_hamiltonian allocates; this call
  * does not: no cudaMalloc, cudaFree or allocating library routine).  Its
  * scratch (index table and accumulators, about 2 MiB) is one static device
- * array per GPU, held from library load until process exit and cleared by
- * every call.  The first call on each device looks up that array's device
- * address; make that first call before any stream capture.  Work is only
- * enqueued on the context's stream; calls that overlap on the GPU share the
- * array and race. */
+ * array per GPU, held from library load until process exit; every call
+ * clears the whole table first.  The first call on each device looks up that
+ * array's device address; make that first call before any stream capture.
+ * The call runs on the context's device (switching to it and back when
+ * another device is current).  Work is only enqueued on the context's
+ * stream; calls that overlap on the GPU share the array and race. */
 int swcs_energy_noalloc(swcs_ctx* ctx, const uint64_t* d_keys, const double* d_amps, int64_t n, double* d_out);
 
 /* Per-kernel device time with CUDA events recorded on the context's stream

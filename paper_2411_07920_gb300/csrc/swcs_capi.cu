@@ -688,13 +688,15 @@ int sweep(swcs_ctx* c, double* d_g, const uint32_t* sel = nullptr) {
 namespace swcs {
 
 // Used by swcs_energy_noalloc (its own translation unit): the loaded
-// Hamiltonian, the context's stream and the energy kernel's grid size.
-int ctx_ham_for_noalloc(swcs_ctx* c, HamDev* H, cudaStream_t* st, int* nblocks) {
+// Hamiltonian, the context's stream, the energy kernel's grid size and the
+// device the context was created on.
+int ctx_ham_for_noalloc(swcs_ctx* c, HamDev* H, cudaStream_t* st, int* nblocks, int* dev) {
   const int r = need_ham(c);
   if (r) return r;
   *H = ham_dev(c);
   *st = c->st;
   *nblocks = c->nsm * sigma_blocks_per_sm();
+  *dev = c->dev;
   return SWCS_OK;
 }
 
