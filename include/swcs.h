@@ -176,6 +176,18 @@ int swcs_set_state(swcs_ctx* ctx, const uint64_t* h_keys, const double* h_amps, 
  * vector the energy kernel forms), with the bitstrings, sorted by bitstring;
  * same size/cap convention as swcs_get_state. */
 int swcs_get_sigma(swcs_ctx* ctx, uint64_t* h_keys, double* h_sigma, int64_t cap, int64_t* n_out);
+/* sigma_E = (H psi)_E = sum_{D in S} <E|H|D> c_D at arbitrary determinants E
+ * of the sector, in or outside the state: the external sigma the pool
+ * gradient contracts (ADAPT step 4, Sec. II.C), read out of the pool sweep's
+ * own alpha-string rows.  The sweep visits only the alpha strings of the
+ * given determinants and scatters only into the row sectors they occupy.
+ *   h_keys   [n] determinants (any order, repeats allowed); a key outside the
+ *            sector (bits >= n_so, wrong electron count, S_z != 0) gives
+ *            SWCS_ERR_INVALID_ARG and nothing is computed
+ *   h_sigma  [n] output, in the order of h_keys
+ * Needs a non-empty state; SWCS_ERR_INVALID_ARG where the row sweep does
+ * not apply (beta-string space above 2^22 strings).  Synchronises. */
+int swcs_sigma_at(swcs_ctx* ctx, const uint64_t* h_keys, int64_t n, double* h_sigma);
 
 /* Diagnostics accumulated since the last swcs_profile_read(.., reset=1):
  * {gates applied, radix-select passes, distinct determinants in the last

@@ -76,6 +76,7 @@ struct swcs_ctx {
 
   // adjoint: checkpoints, per-gate snapshots of one segment, sigma, nu, indices, gradient
   DevBuf ck_keys, ck_amps, ck_n, sn_keys, sn_amps, sn_n, sigma, nu0, nu1, atab0, atab1, dth;
+  DevBuf prb;  // swcs_sigma_at: requested alpha strings, ranges, beta ranks and outputs
 
   // external sigma table
   DevBuf ext;
@@ -477,8 +478,18 @@ __global__ void sincos_kernel(const double* th, double* cs, int n) {
 // Alpha-string row sweep; returns 1 when not applicable (caller falls back).
 // nd_bound >= 0: size buffers for that many determinants instead of reading
 // the state size (no host synchronisation); enqueue = false: only size.
+// Device arrays of a sigma probe (swcs_sigma_at): alpha strings to visit, their
+// ranges of requested beta ranks, and the outputs.
+struct RowProbe {
+  int n = 0;
+  const uint32_t* x = nullptr;
+  const int* off = nullptr;
+  const uint32_t* rank = nullptr;
+  double* out = nullptr;
+};
+
 int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = true, const uint32_t* sel = nullptr,
-               bool energy_only = false, double* sig_out = nullptr) {
+               bool energy_only = false, double* sig_out = nullptr, const RowProbe* probe = nullptr) {
   const int m = c->n / 2;
   if (m > 32 || c->NB <= 0 || c->NB > (1 << 22)) return 1;
   const int64_t nd = nd_bound >= 0 ? nd_bound : host_state_size(c);
@@ -525,7 +536,7 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
   CK(cudaMemsetAsync(c->gfill.p, 0, nd * 8 + 8, c->st));
   CK(cudaMemsetAsync(&k->n_distinct, 0, 8, c->st));
   CK(cudaMemsetAsync(k->acc, 0, 16, c->st));
-  if (!energy_only) CK(cudaMemsetAsync(d_g, 0, sizeof(double) * c->pool_size, c->st));
+  if (!energy_only && !probe) CK(cudaMemsetAsync(d_g, 0, sizeof(double) * c->pool_size, c->st));
   CK(cudaMemsetAsync(c->rows.p, 0, (size_t)ncl * ((c->NB + 3) & ~(int64_t)3) * 8, c->st));  // rows padded to 32 B
   GroupArgs ga;
   ga.keys = (const uint64_t*)c->keys_a.p;
@@ -580,10 +591,16 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
   ra.sig_out = sig_out;
   ra.gorig = (const uint32_t*)c->gorig.p;
   ra.n_groups = ga.n_groups;
+  ra.n_probe = probe ? probe->n : 0;
+  ra.probe_x = probe ? probe->x : nullptr;
+  ra.probe_off = probe ? probe->off : nullptr;
+  ra.probe_rank = probe ? probe->rank : nullptr;
+  ra.probe_out = probe ? probe->out : nullptr;
   CK(launch_k(c, kKRow, [&] { return launch_row_sweep(ra, nthr, c->opt_row_occ, gsz, ncl, smem, c->st); }));
   c->stats[2] = 0;
   c->stats[3] = ncl;
   c->stats[4] = (int64_t)ncl * c->NB;
+  if (probe) return SWCS_OK;
   if (!energy_only) CK(launch_k(c, kKOther, [&] { return launch_scale_gradient(d_g, c->pool_size, k->acc, c->st); }));
   CK(launch_k(c, kKOther, [&] { return launch_finalize_energy(k->acc, k->eout, c->st); }));
   return SWCS_OK;
@@ -738,7 +755,7 @@ int swcs_destroy(swcs_ctx* c) {
                     &c->rbeta, &c->gab, &c->kab, &c->gorig,
                     &c->ck_keys, &c->ck_amps, &c->ck_n, &c->sn_keys, &c->sn_amps, &c->sn_n, &c->sigma, &c->nu0,
                     &c->nu1, &c->atab0, &c->atab1, &c->dth, &c->pool_dev, &c->selbits, &c->feat,
-                    &c->ypred, &c->topk_hist, &c->topk_ctl, &c->occ};
+                    &c->ypred, &c->topk_hist, &c->topk_ctl, &c->occ, &c->prb};
   for (DevBuf* b : bufs) release(*b);
   if (c->pin) cudaFreeHost(c->pin);
   for (auto& e : c->ev_pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
@@ -1248,6 +1265,68 @@ int swcs_get_sigma(swcs_ctx* c, uint64_t* keys, double* sigma, int64_t cap, int6
     keys[i] = kk[ord[i]];
     sigma[i] = ss[ord[i]];
   }
+  return SWCS_OK;
+}
+
+int swcs_sigma_at(swcs_ctx* c, const uint64_t* keys, int64_t n, double* sigma) {
+  int r = need_nonempty(c);
+  if (r) return r;
+  if (n < 0 || (n > 0 && (!keys || !sigma))) return fail(c, SWCS_ERR_INVALID_ARG, "bad sigma_at arrays");
+  if (n == 0) return SWCS_OK;
+  if (n > (int64_t)1 << 30) return fail(c, SWCS_ERR_INVALID_ARG, "too many determinants for sigma_at");
+  const uint64_t valid = c->n >= 64 ? ~0ull : (1ull << c->n) - 1ull;
+  const int m = c->n / 2;
+  // alpha string, beta-string colex rank (sum over occupied spatial orbitals p_i, ascending, of C(p_i, i+1))
+  std::vector<uint32_t> xa(n), rb(n);
+  for (int64_t i = 0; i < n; ++i) {
+    const uint64_t d = keys[i];
+    if (d & ~valid) return fail(c, SWCS_ERR_INVALID_ARG, "determinant %lld has bits >= n_so", (long long)i);
+    if (__builtin_popcountll(d) != c->ne) return fail(c, SWCS_ERR_INVALID_ARG, "determinant %lld has wrong electron count", (long long)i);
+    if (__builtin_popcountll(d & 0x5555555555555555ull) != c->no)
+      return fail(c, SWCS_ERR_INVALID_ARG, "determinant %lld is outside the S_z = 0 sector", (long long)i);
+    uint32_t x = 0, rank = 0;
+    int nb = 0;
+    for (int p = 0; p < m; ++p) {
+      if ((d >> (2 * p)) & 1ull) x |= 1u << p;
+      if ((d >> (2 * p + 1)) & 1ull) rank += (uint32_t)binom(p, ++nb);
+    }
+    xa[i] = x;
+    rb[i] = rank;
+  }
+  std::vector<int64_t> ord(n);
+  for (int64_t i = 0; i < n; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return xa[a] < xa[b]; });
+  std::vector<uint32_t> ux, rk(n);
+  std::vector<int> off;
+  for (int64_t t = 0; t < n; ++t) {
+    if (t == 0 || xa[ord[t]] != xa[ord[t - 1]]) {
+      ux.push_back(xa[ord[t]]);
+      off.push_back((int)t);
+    }
+    rk[t] = rb[ord[t]];
+  }
+  off.push_back((int)n);
+  const int nx = (int)ux.size();
+  const size_t bx = ((size_t)nx * 4 + 15) & ~(size_t)15, bo = ((size_t)(nx + 1) * 4 + 15) & ~(size_t)15;
+  const size_t br = ((size_t)n * 4 + 15) & ~(size_t)15;
+  if ((r = ensure(c, c->prb, bx + bo + br + (size_t)n * 8))) return r;
+  uint8_t* base = (uint8_t*)c->prb.p;
+  RowProbe pr;
+  pr.n = nx;
+  pr.x = (const uint32_t*)base;
+  pr.off = (const int*)(base + bx);
+  pr.rank = (const uint32_t*)(base + bx + bo);
+  pr.out = (double*)(base + bx + bo + br);
+  CK(cudaMemcpyAsync((void*)pr.x, ux.data(), (size_t)nx * 4, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync((void*)pr.off, off.data(), (size_t)(nx + 1) * 4, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync((void*)pr.rank, rk.data(), (size_t)n * 4, cudaMemcpyHostToDevice, c->st));
+  r = sweep_rows(c, nullptr, -1, true, nullptr, false, nullptr, &pr);
+  if (r == 1) return fail(c, SWCS_ERR_INVALID_ARG, "sigma_at needs the alpha-string row sweep (not applicable to this sector)");
+  if (r) return r;
+  std::vector<double> out(n);
+  CK(cudaMemcpyAsync(out.data(), pr.out, (size_t)n * 8, cudaMemcpyDeviceToHost, c->st));
+  if ((r = check_device(c, "swcs_sigma_at"))) return r;
+  for (int64_t t = 0; t < n; ++t) sigma[ord[t]] = out[t];
   return SWCS_OK;
 }
 

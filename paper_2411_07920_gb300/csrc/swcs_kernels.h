@@ -140,6 +140,13 @@ struct RowArgs {
   double* sig_out;
   const uint32_t* gorig;
   const unsigned long long* n_groups;  // groups of the state (energy only: the targets are these alpha strings)
+  // probe mode (n_probe > 0): visit only the listed alpha strings, scatter only into the row sectors of
+  // the listed beta ranks and read those entries back: sigma_E at arbitrary determinants E
+  int n_probe;                 // alpha strings to visit
+  const uint32_t* probe_x;     // [n_probe] the alpha strings
+  const int* probe_off;        // [n_probe + 1] each string's range in probe_rank / probe_out
+  const uint32_t* probe_rank;  // beta-string ranks of the requested determinants
+  double* probe_out;           // sigma of each requested determinant
 };
 
 struct GroupArgs {

@@ -238,7 +238,7 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
   // pair i * m + j in bits 21..30 (rows of at most 2^21 entries)
   const bool packed = A.rbeta_packed != 0;
   const uint32_t rmask = packed ? 0x1FFFFFu : 0x7FFFFFFFu;
-  const bool filt = SCATTER && A.energy_only && dy.touched != nullptr;
+  const bool filt = SCATTER && (A.energy_only || A.n_probe > 0) && dy.touched != nullptr;
   // ---------------- X's own group: diagonal, beta singles, beta-beta doubles; items (determinant, chunk)
   const long long n_items_same = sh.gx_cnt * nch;
   for (long long u = (long long)crank * kRowWarps + warp; u < n_items_same; u += (long long)gsz * kRowWarps) {
@@ -448,11 +448,13 @@ row_sweep_kernel(RowArgs A) {
   double e_acc = 0.0;
   __syncthreads();
 
-  // targets: every alpha string of the sector, or in energy-only mode the alpha strings of the state's
-  // groups (the others hold no determinant whose sigma is read back)
-  const int n_targets = A.energy_only ? (int)*A.n_groups : A.NA;
+  // targets: every alpha string of the sector, in energy-only mode the alpha strings of the state's
+  // groups (the others hold no determinant whose sigma is read back), in probe mode the listed ones
+  const bool probe = A.n_probe > 0;
+  const int n_targets = probe ? A.n_probe : A.energy_only ? (int)*A.n_groups : A.NA;
   for (int xi = cid; xi < n_targets; xi += ncl) {
-    const uint32_t X = A.energy_only ? even_bits(__ldg(&A.gkey[A.goff[xi]])) : A.alpha_list[xi];
+    const uint32_t X = probe ? __ldg(&A.probe_x[xi])
+                             : A.energy_only ? even_bits(__ldg(&A.gkey[A.goff[xi]])) : A.alpha_list[xi];
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
       const bool inr = lane < m;
@@ -474,6 +476,12 @@ row_sweep_kernel(RowArgs A) {
     if (A.energy_only && dy.touched) {  // the entries that will be read back: X's own determinants
       for (long long t = threadIdx.x; t < sh.gx_cnt; t += kRowThreads) {
         const uint32_t rk = __ldg(&A.grank[sh.gx_off + t]);
+        atomicOr(&dy.touched[sector_word(rk)], sector_bit(rk));
+      }
+    }
+    if (probe && dy.touched) {  // the requested entries of X
+      for (int t = __ldg(&A.probe_off[xi]) + threadIdx.x; t < __ldg(&A.probe_off[xi + 1]); t += kRowThreads) {
+        const uint32_t rk = __ldg(&A.probe_rank[t]);
         atomicOr(&dy.touched[sector_word(rk)], sector_bit(rk));
       }
     }
@@ -525,7 +533,11 @@ row_sweep_kernel(RowArgs A) {
     cl.sync();
     row_phase<kRowThreads, true>(A, sh, dy, row, crank, gsz, e_acc);
     cl.sync();
-    if (A.energy_only) {  // sigma_D of the determinants of X's own group
+    if (probe) {  // the requested entries, split over the cluster
+      const int t0 = __ldg(&A.probe_off[xi]), t1 = __ldg(&A.probe_off[xi + 1]);
+      for (int t = t0 + crank * kRowThreads + (int)threadIdx.x; t < t1; t += gsz * kRowThreads)
+        A.probe_out[t] = row[__ldg(&A.probe_rank[t])];
+    } else if (A.energy_only) {  // sigma_D of the determinants of X's own group
       for (long long t = (long long)crank * kRowThreads + threadIdx.x; t < sh.gx_cnt; t += (long long)gsz * kRowThreads) {
         const long long di = sh.gx_off + t;
         const double sg = row[__ldg(&A.grank[di])];

@@ -87,6 +87,7 @@ _SIGS = {
     "swcs_log_abs_dev": ([_vp, _i64, _vp, _vp], _i),
     "swcs_pool_features_dev": ([_vp, _vp], _i),
     "swcs_get_sigma": ([_vp, _vp, _vp, _i64, _p64], _i),
+    "swcs_sigma_at": ([_vp, _vp, _i64, _vp], _i),
     "swcs_pool_screen_dev": ([_vp, _vp, ctypes.c_double, _vp, _p64], _i),
 }
 
@@ -424,6 +425,13 @@ class Context:
         m = ctypes.c_int64()
         self._ck(lib.swcs_get_sigma(self._h, _ptr(k), _ptr(sg), n, ctypes.byref(m)))
         return k[:m.value], sg[:m.value]
+
+    def sigma_at(self, keys):
+        """sigma_E = (H psi)_E at the given determinants (in or outside the state)."""
+        keys = _c(keys, np.uint64)
+        out = np.zeros(max(len(keys), 1), np.float64)
+        self._ck(lib.swcs_sigma_at(self._h, _ptr(keys), len(keys), _ptr(out)))
+        return out[:len(keys)]
 
     def set_state(self, keys, amps):
         keys = _c(keys, np.uint64)

@@ -403,3 +403,45 @@ def test_magnitude_truncated_adjoint_matches_finite_differences():
     assert checked >= M // 2
     # the criterion dropped determinants on this circuit
     assert len(O.apply_ansatz(w.n_so, w.n_e, w.ops, w.theta, 0)[0]) > len(sets0[-1])
+
+
+# ---------------------------------------------------------------- stored values
+def _stored(name):
+    out = {}
+    for line in open(os.path.join(GOLD, name)):
+        if line.startswith("#") or not line.strip():
+            continue
+        key, *vals = line.split()
+        out[key] = vals
+    return out
+
+
+def test_stored_oracle_values_reproduce_and_match_dense_statevector(c1):
+    """tests/golden/so12_e4_oracle.txt (written by make_golden.py from the
+    oracle alone) is a regression pin: the oracle still reproduces it, and its
+    energy, determinant count and largest pool gradients agree with the dense
+    Jordan-Wigner statevector of the same circuit (Eqs. 1-3), which shares no
+    code with the oracle."""
+    w, basis, H = c1
+    st = _stored("so12_e4_oracle.txt")
+    k, a = O.apply_ansatz(w.n_so, w.n_e, w.ops, w.theta, 0)
+    e, n2 = O.energy(w.n_so, w.h, w.g, k, a)
+    g = O.pool_gradients(w.n_so, w.h, w.g, k, a)
+    _, d = O.energy_grad(w.n_so, w.n_e, w.h, w.g, w.ops, w.theta, 0)
+    assert int(st["n_det"][0]) == len(k)
+    assert abs(float(st["energy"][0]) - e) < 1e-14
+    assert abs(float(st["norm2"][0]) - n2) < 1e-14
+    assert np.abs(np.array(st["dtheta"], float) - d).max() < 1e-13
+    top = {int(t.split(":")[0]): float(t.split(":")[1]) for t in st["pool_top"]}
+    assert list(top) == [int(i) for i in np.argsort(-np.abs(g))[:10]]
+    for kk, v in top.items():
+        assert abs(v - g[kk]) < 1e-13
+    # the stored numbers against the dense statevector
+    psi = J.statevector(w.n_so, w.n_e, w.ops, w.theta)
+    assert int(st["n_det"][0]) == int((np.abs(psi) > 0).sum())
+    assert abs(float(st["energy"][0]) - psi[basis] @ H @ psi[basis] / (psi @ psi)) < 1e-13
+    aops = J.annihilators(w.n_so)
+    pool = O.pool_ops(w.n_so)
+    for kk, v in top.items():
+        chi = J.kappa_matrix(aops, pool[kk]) @ psi
+        assert abs(v - 2.0 * (psi[basis] @ H @ chi[basis]) / (psi @ psi)) < 1e-12
