@@ -52,7 +52,7 @@ def parse(argv=None):
     p.add_argument("--rows-l2", type=int, default=0, help="1: cap concurrent rows to about half of L2")
     p.add_argument("--threads", type=int, default=512, help="threads per CTA of the row sweep")
     p.add_argument("--row-clusters", type=int, default=0, help="clusters of the row sweep (0: as many as fit)")
-    p.add_argument("--row-occupancy", type=int, default=3, help="resident 512-thread row-sweep CTAs per SM (2 or 3)")
+    p.add_argument("--row-occupancy", type=int, default=2, help="resident 512-thread row-sweep CTAs per SM (1, 2 or 3)")
     p.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched leg")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     p.add_argument("--no-screen", action="store_true", help="skip the learned-screening leg")
@@ -375,7 +375,7 @@ def aggregate(total_ms, steps, world, device):
 
 
 # the launch the committed row-sweep traffic was captured on: the default workload and launch shape
-TRAFFIC_CAPTURED = dict(n_keep=1_000_000, cluster=2, rows_l2=0, threads=512, row_clusters=0, row_occupancy=3)
+TRAFFIC_CAPTURED = dict(n_keep=1_000_000, cluster=2, rows_l2=0, threads=512, row_clusters=0, row_occupancy=2)
 
 
 def measured_traffic(kernel, args):

@@ -206,7 +206,7 @@ int swcs_stats(swcs_ctx* ctx, int64_t* h_out8);
  *              sector allows, default), 1 probe kernel (connections of each D
  *              looked up in the state's index), 2 rows
  *   "row_occupancy" resident 512-thread CTAs per SM the row sweep is compiled
- *              for: 3 (default, register-capped) or 2
+ *              for: 2 (default, 64 registers), 3 (40 registers) or 1 (no cap)
  *   "wait_timeout_ms"  bound of every device-side wait (default 2000)
  *   "ext_capacity"  hashed sweep: capacity of its first external table (0,
  *              default: from an estimate); a too-small table is regrown

@@ -64,7 +64,7 @@ struct swcs_ctx {
   int opt_cluster = 2;  // CTAs per row cluster
   int opt_rows_l2 = 0;  // cap concurrent rows to about half of L2
   int opt_threads = 512;  // threads per CTA of the row sweep
-  int opt_row_occ = 3;    // resident 512-thread CTAs per SM asked of the compiler (2 or 3)
+  int opt_row_occ = 2;    // resident 512-thread CTAs per SM asked of the compiler (1, 2 or 3)
   double trunc_eps = 0.0;  // magnitude criterion of the truncation (0: off)
   int opt_energy = 0;     // energy: 0 automatic, 1 probe kernel, 2 alpha-string rows
   uint64_t opt_timeout_ns = kTimeoutNs;  // bound of every device-side wait
@@ -1395,7 +1395,7 @@ int swcs_set_option(swcs_ctx* c, const char* name, int64_t value) {
     if (value < 0 || value > 2) return fail(c, SWCS_ERR_INVALID_ARG, "energy must be 0, 1 or 2");
     c->opt_energy = (int)value;
   } else if (k == "row_occupancy") {
-    if (value != 2 && value != 3) return fail(c, SWCS_ERR_INVALID_ARG, "row_occupancy must be 2 or 3");
+    if (value < 1 || value > 3) return fail(c, SWCS_ERR_INVALID_ARG, "row_occupancy must be 1, 2 or 3");
     c->opt_row_occ = (int)value;
   } else if (k == "threads") {
     if (value != 128 && value != 256 && value != 512) return fail(c, SWCS_ERR_INVALID_ARG, "threads must be 128, 256 or 512");

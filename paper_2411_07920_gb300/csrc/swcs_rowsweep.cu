@@ -167,15 +167,6 @@ __device__ __forceinline__ void warp_lists(RowShared& sh, int warp, int lane, ui
   __syncwarp();
 }
 
-// The occupied spin-orbitals of d only (what the Fock element of a single needs).
-__device__ __forceinline__ void warp_occ(RowShared& sh, int warp, int lane, uint64_t d) {
-  const unsigned below = (1u << lane) - 1u;
-  const unsigned lo = (unsigned)d, hi = (unsigned)(d >> 32);
-  if ((lo >> lane) & 1u) sh.occ_all[warp][__popc(lo & below)] = (uint8_t)lane;
-  if ((hi >> lane) & 1u) sh.occ_all[warp][__popc(lo) + __popc(hi & below)] = (uint8_t)(32 + lane);
-  __syncwarp();
-}
-
 // Block-wide exclusive scan, in list order, of the work items of each entry:
 // ceil(group size / chunk).
 template <int kRowThreads>
@@ -270,103 +261,181 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
       }
     }
     const int t_end = min(t_same, (ch + 1) * kSameChunk);
-    for (int t = max(1, ch * kSameChunk) + lane; t < t_end; t += 32) {
+    const int ns1 = 1 + ks * nvs;  // targets 1 .. ns are the beta singles, then the beta-beta doubles
+    for (int t = max(1, ch * kSameChunk) + lane; t < min(t_end, ns1); t += 32) {
+      // beta single: rank and phase precomputed for this determinant
       const uint32_t code = dy.same_tab[t];
-      const int o1 = code & 255, o2 = (code >> 8) & 255, v1 = (code >> 16) & 255, v2 = code >> 24;
-      if (o2 == 255) {  // beta single: rank and phase precomputed for this determinant
-        const int i = sh.bocc[warp][o1], jv = sh.bvir[warp][v1];
-        const uint32_t wb = __ldg(&A.rbeta[(size_t)di * (ks * nvs) + o1 * nvs + v1]);
-        const uint32_t re = wb & rmask;
-        const int sb = (int)(wb >> 31);
-        const int p = 2 * i + 1, r = 2 * jv + 1;
-        if (SCATTER) {
-          if (take(touched, filt, re)) atomicAdd(&row[re], apply_sign(fock_single(A, oa, p, r), sb) * cd);
-        } else {
-          const int k = __ldg(&A.H.ops1[(p < r ? p : r) * A.H.n + (p < r ? r : p)]);
-          if (!A.sel_bits || ((__ldg(&A.sel_bits[k >> 5]) >> (k & 31)) & 1u))
-            atomicAdd(&A.g[k], apply_sign(cd * row[re], sb ^ (int)(p > r)));
-        }
+      const int o1 = code & 255, v1 = (code >> 16) & 255;
+      const int i = sh.bocc[warp][o1], jv = sh.bvir[warp][v1];
+      const uint32_t wb = __ldg(&A.rbeta[(size_t)di * (ks * nvs) + o1 * nvs + v1]);
+      const uint32_t re = wb & rmask;
+      const int sb = (int)(wb >> 31);
+      const int p = 2 * i + 1, r = 2 * jv + 1;
+      if (SCATTER) {
+        if (take(touched, filt, re)) atomicAdd(&row[re], apply_sign(fock_single(A, oa, p, r), sb) * cd);
       } else {
-        const int i1 = sh.bocc[warp][o1], i2 = sh.bocc[warp][o2];
-        const int j1 = sh.bvir[warp][v1], j2 = sh.bvir[warp][v2];
-        const uint32_t re = str_rank(A.rank_tab, ks, db ^ (1u << i1) ^ (1u << i2) ^ (1u << j1) ^ (1u << j2));
-        row_pair<SCATTER>(A, row, touched, filt, d, cd, re, 2 * i1 + 1, 2 * i2 + 1, 2 * j1 + 1, 2 * j2 + 1, oa);
+        const int k = __ldg(&A.H.ops1[(p < r ? p : r) * A.H.n + (p < r ? r : p)]);
+        if (!A.sel_bits || ((__ldg(&A.sel_bits[k >> 5]) >> (k & 31)) & 1u))
+          atomicAdd(&A.g[k], apply_sign(cd * row[re], sb ^ (int)(p > r)));
+      }
+    }
+    // beta-beta doubles, four per lane: every target's loads are issued before the first atomic
+    for (int t0 = max(ns1, ch * kSameChunk); t0 < t_end; t0 += 128) {
+      uint32_t re[4];
+      int ix[4], sg[4];
+      double val[4];
+      bool ok[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int t = t0 + u * 32 + lane;
+        ok[u] = t < t_end;
+        re[u] = 0;
+        ix[u] = 0;
+        sg[u] = 0;
+        val[u] = 0.0;
+        if (!ok[u]) continue;
+        const uint32_t code = dy.same_tab[t];
+        const int i1 = sh.bocc[warp][code & 255], i2 = sh.bocc[warp][(code >> 8) & 255];
+        const int j1 = sh.bvir[warp][(code >> 16) & 255], j2 = sh.bvir[warp][code >> 24];
+        re[u] = str_rank(A.rank_tab, ks, db ^ (1u << i1) ^ (1u << i2) ^ (1u << j1) ^ (1u << j2));
+        if (SCATTER && !take(touched, filt, re[u])) { ok[u] = false; continue; }
+        const int p = 2 * i1 + 1, q = 2 * i2 + 1, r = 2 * j1 + 1, s2 = 2 * j2 + 1;
+        const int pa = pair_index(p, q, A.H.n), pb = pair_index(r, s2, A.H.n);
+        sg[u] = double_phase(d, p, q, r, s2);
+        if (SCATTER) {
+          val[u] = __ldg(&A.H.G[(size_t)pa * A.H.npairs + pb]);
+        } else {
+          const bool down = pa > pb;
+          ix[u] = __ldg(&A.H.opd[down ? (size_t)pb * A.H.npairs + pa : (size_t)pa * A.H.npairs + pb]);
+          sg[u] ^= (int)down;
+          if (A.sel_bits && !((__ldg(&A.sel_bits[ix[u] >> 5]) >> (ix[u] & 31)) & 1u)) { ok[u] = false; continue; }
+          val[u] = row[re[u]];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (!ok[u]) continue;
+        if (SCATTER) atomicAdd(&row[re[u]], apply_sign(val[u], sg[u]) * cd);
+        else atomicAdd(&A.g[ix[u]], apply_sign(cd * val[u], sg[u]));
       }
     }
     __syncwarp();
   }
-  // ---------------- alpha-single neighbours: alpha single + alpha-beta doubles (warp per determinant)
-  int e = 0;  // a warp's items only increase: walk its entry forward instead of searching
-  for (uint32_t t = warp; t < sh.tot_s; t += kRowWarps) {
-    while (e + 1 < sh.n_s && dy.ents_s[e + 1].flat <= t) ++e;
-    const RowEnt en = dy.ents_s[e];
+  // ---------------- alpha-single neighbours, the alpha single itself: one determinant per lane.  Each
+  // lane sums its own Fock element h_qp + sum_{k in D} <qk||pk> (no warp reduction per determinant)
+  for (uint32_t t0 = (uint32_t)warp * 32; t0 < sh.tot_s; t0 += kRowThreads) {
+    int e1 = warp_find_entry(dy.ents_s, sh.n_s, t0, lane);
+    const int ej = e1 + lane;
+    const uint32_t st = (lane > 0 && ej < sh.n_s) ? dy.ents_s[ej].flat - t0 : 32u;
+    const unsigned starts = __reduce_or_sync(0xffffffffu, st < 32u ? 1u << st : 0u);
+    e1 += __popc(starts & ((2u << lane) - 1u));
+    const uint32_t t = t0 + lane;
+    if (t >= sh.tot_s) continue;
+    while (e1 + 1 < sh.n_s && dy.ents_s[e1 + 1].flat <= t) ++e1;
+    const RowEnt en = dy.ents_s[e1];
     const long long di = (long long)en.off + (t - en.flat);
-    const uint64_t d = __ldg(&A.gkey[di]);
-    const double cd = __ldg(&A.gamp[di]);
-    // packed beta-single entries need no beta lists; the gather needs no occupied list either
-    if (!packed) warp_lists(sh, warp, lane, d, m);
-    else if (SCATTER) warp_occ(sh, warp, lane, d);
-    const uint8_t* oa = sh.occ_all[warp];
+    const uint32_t rd = __ldg(&A.grank[di]);
     const int pa = en.o[0], pb = en.o[2];  // alpha spin-orbitals: removed, added
-    if (SCATTER) {  // the alpha single itself: its Fock element summed across the warp
-      const uint32_t rd = __ldg(&A.grank[di]);
-      if (!filt || (touched[sector_word(rd)] & sector_bit(rd))) {  // the same word for every lane
-        const int n = A.H.n;
-        const double* w = A.H.Ws + ((size_t)pa * n + pb) * n;
-        double f = 0.0;
-        for (int t3 = lane; t3 < A.H.ne; t3 += 32) f += __ldg(&w[oa[t3]]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
-        if (lane == 0 && take(touched, filt, rd))
-          atomicAdd(&row[rd], apply_sign(__ldg(&A.H.h[pb * n + pa]) + f, single_phase(d, pa, pb)) * cd);
-      }
-    } else if (lane == 0) {
-      row_pair<SCATTER>(A, row, touched, filt, d, cd, __ldg(&A.grank[di]), pa, -1, pb, -1, oa);
+    if (SCATTER) {
+      if (!take(touched, filt, rd)) continue;
+      const uint64_t d = __ldg(&A.gkey[di]);
+      const double cd = __ldg(&A.gamp[di]);
+      const int n = A.H.n;
+      const double* wv = A.H.Ws + ((size_t)pa * n + pb) * n;
+      double f = __ldg(&A.H.h[pb * n + pa]);
+      for (uint64_t x = d; x; x &= x - 1ull) f += __ldg(&wv[__ffsll((long long)x) - 1]);
+      atomicAdd(&row[rd], apply_sign(f, single_phase(d, pa, pb)) * cd);
+    } else {
+      row_pair<SCATTER>(A, row, touched, filt, __ldg(&A.gkey[di]), __ldg(&A.gamp[di]), rd, pa, -1, pb, -1, nullptr);
     }
-    // alpha-beta doubles: phase = (beta single on D) ^ (alpha single on D) ^ (index-only bit in the tables)
+  }
+  // ---------------- alpha-single neighbours, alpha-beta doubles (warp per determinant).
+  // Software pipeline over a warp's items: the next item's determinant, amplitude and first 128
+  // beta-single entries are loaded while the current one is processed, so the item's chain of dependent
+  // loads (state -> beta-single list -> integral -> row) overlaps the previous item's work.
+  const int nsb = ks * nvs;
+  int e = 0;  // entry of the prefetched item: a warp's items only increase, so walk forward
+  long long di_n = 0;
+  uint64_t d_n = 0;
+  double cd_n = 0.0;
+  uint32_t wb_n[4] = {0u, 0u, 0u, 0u};
+  auto fetch = [&](uint32_t tt) {
+    while (e + 1 < sh.n_s && dy.ents_s[e + 1].flat <= tt) ++e;
+    const RowEnt en = dy.ents_s[e];
+    di_n = (long long)en.off + (tt - en.flat);
+    d_n = __ldg(&A.gkey[di_n]);
+    cd_n = __ldg(&A.gamp[di_n]);
+    const uint32_t* rb = A.rbeta + (size_t)di_n * nsb;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int t2 = u * 32 + lane;
+      wb_n[u] = t2 < nsb ? __ldg(&rb[t2]) : 0u;
+    }
+  };
+  if ((uint32_t)warp < sh.tot_s) fetch((uint32_t)warp);
+  for (uint32_t t = warp; t < sh.tot_s; t += kRowWarps) {
+    const RowEnt en = dy.ents_s[e];
+    const long long di = di_n;
+    const uint64_t d = d_n;
+    const double cd = cd_n;
+    uint32_t wb0[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) wb0[u] = wb_n[u];
+    if (t + kRowWarps < sh.tot_s) fetch(t + kRowWarps);
+    if (!packed) warp_lists(sh, warp, lane, d, m);  // unpacked entries: pair indices from the beta lists
+    const int pa = en.o[0], pb = en.o[2];  // alpha spin-orbitals: removed, added
+    // alpha-beta doubles: phase = (beta single on D) ^ (alpha single on D) ^ (index-only bit in the tables);
+    // four targets per lane with their loads issued together
     const int sa = single_phase(d, pa, pb);
     const size_t base = ((size_t)(pa >> 1) * m + (pb >> 1)) * (size_t)m * m;
-    const uint32_t* rb = A.rbeta + (size_t)di * (ks * nvs);
-    const int nsb = ks * nvs;
-    if (SCATTER) {
-      if (filt) {  // energy only: almost every target is skipped, so test before loading the integral
-        for (int t2 = lane; t2 < nsb; t2 += 32) {
-          const uint32_t wb = __ldg(&rb[t2]);
-          const uint32_t re = wb & rmask;
-          if (!take(touched, true, re)) continue;
-          const uint32_t ij = packed ? (wb >> 21) & 1023u : (uint32_t)(sh.bocc[warp][t2 / nvs] * m + sh.bvir[warp][t2 % nvs]);
-          atomicAdd(&row[re], apply_sign(__ldg(&A.gab[base + ij]), (int)(wb >> 31) ^ sa) * cd);
-        }
-      } else {  // both loads issued up front, off the atomic's dependency chain
-        for (int t2 = lane; t2 < nsb; t2 += 32) {
-          const uint32_t wb = __ldg(&rb[t2]);
-          const uint32_t ij = packed ? (wb >> 21) & 1023u : (uint32_t)(sh.bocc[warp][t2 / nvs] * m + sh.bvir[warp][t2 % nvs]);
-          const double gv = __ldg(&A.gab[base + ij]);
-          const uint32_t re = wb & rmask;
-          take(touched, false, re);
-          atomicAdd(&row[re], apply_sign(gv, (int)(wb >> 31) ^ sa) * cd);
-        }
+    const uint32_t* rb = A.rbeta + (size_t)di * nsb;
+    for (int t0 = 0; t0 < nsb; t0 += 128) {
+      uint32_t wv[4];
+      bool ok[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int t2 = t0 + u * 32 + lane;
+        ok[u] = t2 < nsb;
+        wv[u] = t0 == 0 ? wb0[u] : (ok[u] ? __ldg(&rb[t2]) : 0u);
       }
-    } else {
-      // four targets per lane with their row reads issued together
-      for (int t0 = 0; t0 < nsb; t0 += 128) {
+      auto pair_ij = [&](int u) -> uint32_t {
+        const int t2 = t0 + u * 32 + lane;
+        return packed ? (wv[u] >> 21) & 1023u : (uint32_t)(sh.bocc[warp][t2 / nvs] * m + sh.bvir[warp][t2 % nvs]);
+      };
+      if (SCATTER) {
+        if (filt) {  // energy only: almost every target is skipped, so test before loading the integral
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (!ok[u]) continue;
+            const uint32_t re = wv[u] & rmask;
+            if (!take(touched, true, re)) continue;
+            atomicAdd(&row[re], apply_sign(__ldg(&A.gab[base + pair_ij(u)]), (int)(wv[u] >> 31) ^ sa) * cd);
+          }
+        } else {  // the four integral loads issued up front, off the atomics' dependency chain
+          double gv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) gv[u] = ok[u] ? __ldg(&A.gab[base + pair_ij(u)]) : 0.0;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (!ok[u]) continue;
+            const uint32_t re = wv[u] & rmask;
+            take(touched, false, re);
+            atomicAdd(&row[re], apply_sign(gv[u], (int)(wv[u] >> 31) ^ sa) * cd);
+          }
+        }
+      } else {
         uint32_t re[4];
         int kk[4], sb[4];
         double sv[4];
-        bool ok[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int t2 = t0 + u * 32 + lane;
-          ok[u] = t2 < nsb;
           re[u] = 0;
           kk[u] = 0;
           sb[u] = 0;
           if (ok[u]) {
-            const uint32_t wb = __ldg(&rb[t2]);
-            const uint32_t ij = packed ? (wb >> 21) & 1023u : (uint32_t)(sh.bocc[warp][t2 / nvs] * m + sh.bvir[warp][t2 % nvs]);
-            re[u] = wb & rmask;
-            sb[u] = (int)(wb >> 31) ^ sa;
-            kk[u] = __ldg(&A.kab[base + ij]);
+            re[u] = wv[u] & rmask;
+            sb[u] = (int)(wv[u] >> 31) ^ sa;
+            kk[u] = __ldg(&A.kab[base + pair_ij(u)]);
             const int k = kk[u] & 0x7FFFFFFF;
             if (A.sel_bits && !((__ldg(&A.sel_bits[k >> 5]) >> (k & 31)) & 1u)) ok[u] = false;
           }
@@ -383,20 +452,51 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
   // ---------------- alpha-double neighbours: one determinant per lane; the warp finds the entry of
   // its first item, then each lane counts the entries that start at or before its own item (lane j
   // marks where entry e + j starts inside the warp's 32 items: groups hold at least one determinant,
-  // so the starts are distinct and the walk below takes no step)
+  // so the starts are distinct and the walk below takes no step).  Every item of an entry is the same
+  // pool operator, so the gather sums each entry's lanes in the warp and its first lane adds the total.
+  const int npairs = A.H.npairs, n = A.H.n;
   for (uint32_t t0 = (uint32_t)warp * 32; t0 < sh.tot_d; t0 += kRowThreads) {
     int e = warp_find_entry(dy.ents_d, sh.n_d, t0, lane);
     const int ej = e + lane;
     const uint32_t st = (lane > 0 && ej < sh.n_d) ? dy.ents_d[ej].flat - t0 : 32u;
-    const unsigned starts = __reduce_or_sync(0xffffffffu, st < 32u ? 1u << st : 0u);
-    e += __popc(starts & ((2u << lane) - 1u));
+    const unsigned starts = __reduce_or_sync(0xffffffffu, st < 32u ? 1u << st : 0u) | 1u;
+    e += __popc(starts & ((2u << lane) - 1u) & ~1u);
     const uint32_t t = t0 + lane;
-    if (t < sh.tot_d) {
-      while (e + 1 < sh.n_d && dy.ents_d[e + 1].flat <= t) ++e;
+    const bool live = t < sh.tot_d;
+    double v = 0.0;
+    int k = -1;
+    if (live) {
       const RowEnt en = dy.ents_d[e];
       const long long di = (long long)en.off + (t - en.flat);
-      row_pair<SCATTER>(A, row, touched, filt, __ldg(&A.gkey[di]), __ldg(&A.gamp[di]), __ldg(&A.grank[di]), en.o[0],
-                        en.o[1], en.o[2], en.o[3], nullptr);
+      const int p = en.o[0], q = en.o[1], r = en.o[2], s2 = en.o[3];
+      const int pa = pair_index(p, q, n), pb = pair_index(r, s2, n);
+      const uint32_t rd = __ldg(&A.grank[di]);
+      if (SCATTER) {
+        if (take(touched, filt, rd)) {
+          const double gv = __ldg(&A.H.G[(size_t)pa * npairs + pb]);
+          const uint64_t d = __ldg(&A.gkey[di]);
+          const double cd = __ldg(&A.gamp[di]);
+          atomicAdd(&row[rd], apply_sign(gv, double_phase(d, p, q, r, s2)) * cd);
+        }
+      } else {
+        const bool down = pa > pb;
+        k = __ldg(&A.H.opd[down ? (size_t)pb * npairs + pa : (size_t)pa * npairs + pb]);
+        if (A.sel_bits && !((__ldg(&A.sel_bits[k >> 5]) >> (k & 31)) & 1u)) k = -1;
+        const uint64_t d = __ldg(&A.gkey[di]);
+        const double cd = __ldg(&A.gamp[di]);
+        if (k >= 0) v = apply_sign(cd * row[rd], double_phase(d, p, q, r, s2) ^ (int)down);
+      }
+    }
+    if (!SCATTER) {
+      // segmented sum over the lanes of each entry: lane + o is added while it is in the same entry
+      const unsigned later = starts & ~((2u << lane) - 1u);  // starts after this lane
+      const int seg_end = later ? __ffs(later) - 1 : 32;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const double w = __shfl_down_sync(0xffffffffu, v, o);
+        if (lane + o < seg_end) v += w;
+      }
+      if (live && k >= 0 && ((starts >> lane) & 1u) && v != 0.0) atomicAdd(&A.g[k], v);
     }
   }
 }
@@ -745,12 +845,13 @@ cudaError_t launch_t(const RowArgs& a, int gsz, int n_clusters, size_t smem, cud
 }  // namespace
 
 // threads: 128, 256 or 512 per CTA; resident 512-thread CTAs per SM requested
-// from the compiler: 2 (no register cap) or 3 (40 registers)
+// from the compiler: 1 (no register cap), 2 (64 registers) or 3 (40 registers)
 cudaError_t row_sweep_max_clusters(int threads, int occ, int gsz, size_t smem, int* n_clusters) {
   if (threads == 128) return max_clusters_t<128, 1>(gsz, smem, n_clusters);
   if (threads == 256) return max_clusters_t<256, 1>(gsz, smem, n_clusters);
   if (threads == 512) return occ >= 3 ? max_clusters_t<512, 3>(gsz, smem, n_clusters)
-                                      : max_clusters_t<512, 1>(gsz, smem, n_clusters);
+                             : occ == 2 ? max_clusters_t<512, 2>(gsz, smem, n_clusters)
+                                        : max_clusters_t<512, 1>(gsz, smem, n_clusters);
   return cudaErrorInvalidValue;
 }
 
@@ -759,7 +860,8 @@ cudaError_t launch_row_sweep(const RowArgs& a, int threads, int occ, int gsz, in
   if (threads == 128) return launch_t<128, 1>(a, gsz, n_clusters, smem, st);
   if (threads == 256) return launch_t<256, 1>(a, gsz, n_clusters, smem, st);
   if (threads == 512) return occ >= 3 ? launch_t<512, 3>(a, gsz, n_clusters, smem, st)
-                                      : launch_t<512, 1>(a, gsz, n_clusters, smem, st);
+                             : occ == 2 ? launch_t<512, 2>(a, gsz, n_clusters, smem, st)
+                                        : launch_t<512, 1>(a, gsz, n_clusters, smem, st);
   return cudaErrorInvalidValue;
 }
 

@@ -34,7 +34,7 @@ def test_committed_traffic_is_reported_only_for_the_captured_launch():
     text = open(os.path.join(ROOT, "profiles", "row_sweep_so52_e12_N1e6.md")).read()
     committed = int(text.split("traffic_bytes_per_launch:")[1].split()[0])
     assert bench.measured_traffic("row_sweep", bench.parse([])) in (committed, None)
-    for argv in (["--n-keep", "300000"], ["--threads", "256"], ["--cluster", "1"], ["--row-occupancy", "2"],
+    for argv in (["--n-keep", "300000"], ["--threads", "256"], ["--cluster", "1"], ["--row-occupancy", "3"],
                  ["--rows-l2", "1"], ["--sweep", "1"]):
         assert bench.measured_traffic("row_sweep", bench.parse(argv)) is None, argv
     assert bench.measured_traffic("ansatz", bench.parse([])) is None
