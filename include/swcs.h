@@ -149,6 +149,22 @@ int swcs_energy_dev(swcs_ctx* ctx, double* d_out);
  * other operator (sigma itself is still formed in full). */
 int swcs_pool_gradients(swcs_ctx* ctx, double* h_g_out, const int64_t* h_subset, int64_t n_subset);
 int swcs_pool_gradients_dev(swcs_ctx* ctx, double* d_g_out, const int64_t* d_subset, int64_t n_subset);
+/* One shard of the pool sweep for a run over n_shards GPUs (one process per
+ * GPU, each holding the same state).  The shards partition the external
+ * determinants E by the colex rank of their alpha string (rank mod n_shards
+ * = shard), so every sigma_E is formed by exactly one shard and a single
+ * sum over the shards completes the sweep (ADAPT step 4, Sec. II.C, spread
+ * over devices):
+ *   d_graw  [pool_size] device: sum over this shard's connected pairs of
+ *           dir * phase * c_D * sigma_E (the gradient before its factor
+ *           2/<psi|psi>), overwritten
+ *   d_acc   [2] device: this shard's part of sum_D c_D sigma_D (the energy
+ *           numerator), and <psi|psi> (the whole state's, the same on every shard)
+ * After an all-reduce (sum) of d_graw and d_acc[0] over the shards:
+ * g = 2 d_graw / d_acc[1], E = d_acc[0] / d_acc[1].  Only enqueues work on the
+ * context's stream.  SWCS_ERR_INVALID_ARG unless 0 <= shard < n_shards, or
+ * where the alpha-string row sweep does not apply. */
+int swcs_pool_gradients_partial_dev(swcs_ctx* ctx, int shard, int n_shards, double* d_graw, double* d_acc);
 /* The pool sweep forms sigma on every determinant of the state as well, so it
  * also yields E = <psi|H|psi>/<psi|psi>: returns that value from the last
  * swcs_pool_gradients* call (synchronises). */

@@ -488,8 +488,15 @@ struct RowProbe {
   double* out = nullptr;
 };
 
+// A shard of the pool sweep (swcs_pool_gradients_partial_dev): target alpha strings of colex rank
+// shard (mod n_shards); the gradient is left unscaled and the energy unfinished.
+struct RowShard {
+  int shard = 0, n_shards = 1;
+};
+
 int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = true, const uint32_t* sel = nullptr,
-               bool energy_only = false, double* sig_out = nullptr, const RowProbe* probe = nullptr) {
+               bool energy_only = false, double* sig_out = nullptr, const RowProbe* probe = nullptr,
+               const RowShard* shard = nullptr) {
   const int m = c->n / 2;
   if (m > 32 || c->NB <= 0 || c->NB > (1 << 22)) return 1;
   const int64_t nd = nd_bound >= 0 ? nd_bound : host_state_size(c);
@@ -596,11 +603,13 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
   ra.probe_off = probe ? probe->off : nullptr;
   ra.probe_rank = probe ? probe->rank : nullptr;
   ra.probe_out = probe ? probe->out : nullptr;
+  ra.shard = shard ? shard->shard : 0;
+  ra.n_shards = shard ? shard->n_shards : 1;
   CK(launch_k(c, kKRow, [&] { return launch_row_sweep(ra, nthr, c->opt_row_occ, gsz, ncl, smem, c->st); }));
   c->stats[2] = 0;
   c->stats[3] = ncl;
   c->stats[4] = (int64_t)ncl * c->NB;
-  if (probe) return SWCS_OK;
+  if (probe || shard) return SWCS_OK;
   if (!energy_only) CK(launch_k(c, kKOther, [&] { return launch_scale_gradient(d_g, c->pool_size, k->acc, c->st); }));
   CK(launch_k(c, kKOther, [&] { return launch_finalize_energy(k->acc, k->eout, c->st); }));
   return SWCS_OK;
@@ -1116,6 +1125,21 @@ int swcs_pool_gradients_dev(swcs_ctx* c, double* d_g_out, const int64_t* d_subse
   }
   if ((r = sweep(c, g, sel))) return r;
   if (d_subset) CK(launch_k(c, kKOther, [&] { return launch_gather_subset(g, d_subset, n_subset, d_g_out, c->st); }));
+  return SWCS_OK;
+}
+
+int swcs_pool_gradients_partial_dev(swcs_ctx* c, int shard, int n_shards, double* d_graw, double* d_acc) {
+  int r = need_nonempty(c);
+  if (r) return r;
+  if (!d_graw || !d_acc) return fail(c, SWCS_ERR_INVALID_ARG, "null output");
+  if (n_shards < 1 || shard < 0 || shard >= n_shards) return fail(c, SWCS_ERR_INVALID_ARG, "shard must be in 0..n_shards-1");
+  RowShard sh;
+  sh.shard = shard;
+  sh.n_shards = n_shards;
+  r = sweep_rows(c, d_graw, -1, true, nullptr, false, nullptr, nullptr, &sh);
+  if (r == 1) return fail(c, SWCS_ERR_INVALID_ARG, "the sharded sweep needs the alpha-string row sweep (not applicable to this sector)");
+  if (r) return r;
+  CK(cudaMemcpyAsync(d_acc, ctrl(c)->acc, 16, cudaMemcpyDeviceToDevice, c->st));
   return SWCS_OK;
 }
 

@@ -147,6 +147,9 @@ struct RowArgs {
   const int* probe_off;        // [n_probe + 1] each string's range in probe_rank / probe_out
   const uint32_t* probe_rank;  // beta-string ranks of the requested determinants
   double* probe_out;           // sigma of each requested determinant
+  // sharded pool sweep (n_shards > 1): only the target alpha strings of colex rank = shard (mod n_shards),
+  // i.e. every E whose alpha string that rank owns; g and acc[0] are then that shard's partial sums
+  int shard, n_shards;
 };
 
 struct GroupArgs {

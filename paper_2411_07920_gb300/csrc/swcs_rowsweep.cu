@@ -552,7 +552,13 @@ row_sweep_kernel(RowArgs A) {
   // groups (the others hold no determinant whose sigma is read back), in probe mode the listed ones
   const bool probe = A.n_probe > 0;
   const int n_targets = probe ? A.n_probe : A.energy_only ? (int)*A.n_groups : A.NA;
-  for (int xi = cid; xi < n_targets; xi += ncl) {
+  // a shard of the pool sweep visits the alpha strings xi = shard (mod n_shards) only (alpha_list is in
+  // colex order, so xi is the string's rank)
+  const int n_sh = (probe || A.energy_only || A.n_shards < 1) ? 1 : A.n_shards;
+  const int sh0 = n_sh > 1 ? A.shard : 0;
+  const int n_own = n_targets > sh0 ? (n_targets - sh0 + n_sh - 1) / n_sh : 0;
+  for (int jx = cid; jx < n_own; jx += ncl) {
+    const int xi = sh0 + jx * n_sh;
     const uint32_t X = probe ? __ldg(&A.probe_x[xi])
                              : A.energy_only ? even_bits(__ldg(&A.gkey[A.goff[xi]])) : A.alpha_list[xi];
     if (threadIdx.x < 32) {

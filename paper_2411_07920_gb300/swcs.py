@@ -88,6 +88,7 @@ _SIGS = {
     "swcs_pool_features_dev": ([_vp, _vp], _i),
     "swcs_get_sigma": ([_vp, _vp, _vp, _i64, _p64], _i),
     "swcs_sigma_at": ([_vp, _vp, _i64, _vp], _i),
+    "swcs_pool_gradients_partial_dev": ([_vp, _i, _i, _vp, _vp], _i),
     "swcs_pool_screen_dev": ([_vp, _vp, ctypes.c_double, _vp, _p64], _i),
 }
 
@@ -395,6 +396,11 @@ class Context:
     def pool_gradients_dev(self, d_g, d_subset=None):
         n = 0 if d_subset is None else int(d_subset.numel())
         self._ck(lib.swcs_pool_gradients_dev(self._h, _tptr(d_g), _tptr(d_subset), n))
+
+    def pool_gradients_partial_dev(self, shard, n_shards, d_graw, d_acc):
+        """One shard of the pool sweep: unscaled partial gradient into d_graw and
+        (partial energy numerator, <psi|psi>) into d_acc (device tensors)."""
+        self._ck(lib.swcs_pool_gradients_partial_dev(self._h, int(shard), int(n_shards), _tptr(d_graw), _tptr(d_acc)))
 
     def energy_grad(self, ops, theta, n_keep, ckpt_every=20):
         ops = _c(ops, np.uint8).reshape(-1)

@@ -21,6 +21,8 @@ import pytest
 import oracle as O
 from paper_2411_07920_gb300 import inputs as I
 
+import pool_ref as R
+
 pytestmark = pytest.mark.gpu
 TOL = 1e-10
 
@@ -200,40 +202,6 @@ def test_external_sigma_sampled_at_full_size(full):
     assert np.abs(want).max() > 1e-6  # the samples carry real contributions
 
 
-def _tau(op, d):
-    """(sign, tau d) or None for the pool operator op = (kind, i0..i3) on the integer d."""
-    kind, i0, i1, i2, i3 = (int(x) for x in op)
-    ann, cre = ([i0], [i1]) if kind == 1 else ([i0, i1], [i2, i3])
-    par = 0
-    for p in ann:  # a_{i0} first, then a_{i1}
-        if not (d >> p) & 1:
-            return None
-        par ^= bin(d & ((1 << p) - 1)).count("1") & 1
-        d ^= 1 << p
-    for p in reversed(cre):  # then a+_{i3}, a+_{i2} (a+_{i1} for singles)
-        if (d >> p) & 1:
-            return None
-        par ^= bin(d & ((1 << p) - 1)).count("1") & 1
-        d |= 1 << p
-    return (-1.0 if par else 1.0), d
-
-
-def _tau_dag(op, d):
-    kind, i0, i1, i2, i3 = (int(x) for x in op)
-    inv = np.array([kind, i1, i0, 0, 0]) if kind == 1 else np.array([kind, i2, i3, i0, i1])
-    return _tau(inv, d)
-
-
-def _support(op, k):
-    """Indices of the determinants on which tau or tau^dag of the pool operator op acts."""
-    kind, i0, i1, i2, i3 = (int(x) for x in op)
-    lo = np.uint64((1 << i0) | (1 << i1) if kind == 2 else 1 << i0)
-    hi = np.uint64((1 << i2) | (1 << i3) if kind == 2 else 1 << i1)
-    up = ((k & lo) == lo) & ((k & hi) == 0)
-    dn = ((k & hi) == hi) & ((k & lo) == 0)
-    return np.nonzero(up | dn)[0]
-
-
 def test_pool_gradient_from_sweep_sigma_at_full_size(full):
     """g_k = 2/<psi|psi> sum_D c_D (s sigma(tau_k D) - s' sigma(tau_k^dag D)),
     contracted on the host from the sweep rows' sigma at every needed E, for
@@ -245,14 +213,14 @@ def test_pool_gradient_from_sweep_sigma_at_full_size(full):
     n2 = float(a @ a)
     rng = np.random.default_rng(12)
     cand = rng.choice(len(pool), 400, replace=False)
-    sizes = [len(_support(pool[kk], k)) for kk in cand]
+    sizes = [len(R.support(pool[kk], k)) for kk in cand]
     order = np.argsort(sizes)
     picks = [int(cand[i]) for i in order if sizes[i] > 0][:3]
     for kk in picks:
         terms, dets = [], []
-        supp = _support(pool[kk], k)
+        supp = R.support(pool[kk], k)
         for d, cd in zip(k[supp], a[supp]):
-            for f, sgn in ((_tau, 1.0), (_tau_dag, -1.0)):
+            for f, sgn in ((R.tau, 1.0), (R.tau_dag, -1.0)):
                 t = f(pool[kk], int(d))
                 if t is not None:
                     terms.append(sgn * t[0] * cd)
