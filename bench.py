@@ -419,6 +419,10 @@ def run_screen_leg(swcs, ctx, w, args, torch, frac=0.05):
     best = min(res, key=lambda r: r["t_screened"])
     best["t_full"] = min(r["t_full"] for r in res)
     best["speedup"] = best["t_full"] / best["t_screened"]
+    # the same subset sweep forming sigma in full (only the contractions filtered), for comparison
+    ctx.set_option("screen_scatter", 0)
+    t_sigma_full = min(screen.evaluate(ctx, net, frac)["t_screened"] for _ in range(3))
+    ctx.set_option("screen_scatter", 1)
     # network forward over the whole pool, device time
     P = ctx.pool_size()
     x = torch.empty((P, 32), dtype=torch.int16, device="cuda")
@@ -449,6 +453,7 @@ def run_screen_leg(swcs, ctx, w, args, torch, frac=0.05):
             "recall_top10": best["recall_top10"], "same_argmax": bool(best["same_argmax"]),
             "max_abs_err_on_subset": best["max_abs_err_on_subset"], "full_ms": round(1e3 * best["t_full"], 3),
             "screened_ms": round(1e3 * best["t_screened"], 3), "speedup": round(best["speedup"], 3),
+            "screened_sigma_in_full_ms": round(1e3 * t_sigma_full, 3),
             "train_s": round(t_train, 2), "train_samples": int(X.shape[0]), "train_loss": hist[-1][1],
             "mlp_forward": {"kernel": "mlp_fused_kernel", "ms": round(1e3 * t_fwd, 4),
                             "tflops": round(flops / t_fwd / 1e12, 2),

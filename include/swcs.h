@@ -145,8 +145,13 @@ int swcs_energy_dev(swcs_ctx* ctx, double* d_out);
  * for the canonical pool (ADAPT step 4, Sec. II.C).  h_subset == NULL:
  * all pool entries are written to h_g_out[pool_size]; otherwise only
  * h_g_out[h_subset[i]] for i < n_subset (other entries untouched).  With a
- * subset the alpha-string row sweep skips the gradient contractions of every
- * other operator (sigma itself is still formed in full). */
+ * subset the device variant's alpha-string row sweep first marks, for each
+ * target alpha string, the row sectors that the selected operators read (and
+ * those of the state's own determinants, so the energy stays exact), forms
+ * sigma only there -- every other connected pair is skipped before its
+ * integral is loaded -- and contracts only the selected operators (option
+ * "screen_scatter" 0: form sigma in full, filter the contractions only).
+ * The host variant evaluates the whole pool and copies the subset out. */
 int swcs_pool_gradients(swcs_ctx* ctx, double* h_g_out, const int64_t* h_subset, int64_t n_subset);
 int swcs_pool_gradients_dev(swcs_ctx* ctx, double* d_g_out, const int64_t* d_subset, int64_t n_subset);
 /* One shard of the pool sweep for a run over n_shards GPUs (one process per
@@ -232,6 +237,9 @@ int swcs_stats(swcs_ctx* ctx, int64_t* h_out8);
  *              SWCS_ERR_TIMEOUT and the context stays usable
  *   "gate_blocks"   CTAs of the persistent gate kernel (0, default: whole device)
  *   "row_clusters"  clusters of the row sweep (0, default: as many as fit)
+ *   "screen_scatter" subset sweeps of swcs_pool_gradients_dev: 1 (default)
+ *              scatter sigma only into the sectors the subset reads, 0 form
+ *              sigma in full
  *   "rows_l2"  1: cap the row sweep's concurrent rows to about half of L2;
  *              0 (default): as many rows as clusters fit on the device */
 int swcs_set_option(swcs_ctx* ctx, const char* name, int64_t value);

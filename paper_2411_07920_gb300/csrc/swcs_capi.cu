@@ -77,6 +77,9 @@ struct swcs_ctx {
   // adjoint: checkpoints, per-gate snapshots of one segment, sigma, nu, indices, gradient
   DevBuf ck_keys, ck_amps, ck_n, sn_keys, sn_amps, sn_n, sigma, nu0, nu1, atab0, atab1, dth;
   DevBuf prb;  // swcs_sigma_at: requested alpha strings, ranges, beta ranks and outputs
+  DevBuf ab_cnt, ab_list;  // screened sweep: selected alpha-beta doubles per alpha pair
+  int opt_screen_scatter = 1;  // a subset sweep marks and scatters only what the selected operators read
+  bool screen_now = false;     // set around a subset sweep whose lists are built
 
   // external sigma table
   DevBuf ext;
@@ -605,6 +608,9 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
   ra.probe_out = probe ? probe->out : nullptr;
   ra.shard = shard ? shard->shard : 0;
   ra.n_shards = shard ? shard->n_shards : 1;
+  ra.screen = (sel && c->screen_now && twords > 0) ? 1 : 0;
+  ra.ab_cnt = (const int*)c->ab_cnt.p;
+  ra.ab_list = (const uint2*)c->ab_list.p;
   CK(launch_k(c, kKRow, [&] { return launch_row_sweep(ra, nthr, c->opt_row_occ, gsz, ncl, smem, c->st); }));
   c->stats[2] = 0;
   c->stats[3] = ncl;
@@ -764,7 +770,7 @@ int swcs_destroy(swcs_ctx* c) {
                     &c->rbeta, &c->gab, &c->kab, &c->gorig,
                     &c->ck_keys, &c->ck_amps, &c->ck_n, &c->sn_keys, &c->sn_amps, &c->sn_n, &c->sigma, &c->nu0,
                     &c->nu1, &c->atab0, &c->atab1, &c->dth, &c->pool_dev, &c->selbits, &c->feat,
-                    &c->ypred, &c->topk_hist, &c->topk_ctl, &c->occ, &c->prb};
+                    &c->ypred, &c->topk_hist, &c->topk_ctl, &c->occ, &c->prb, &c->ab_cnt, &c->ab_list};
   for (DevBuf* b : bufs) release(*b);
   if (c->pin) cudaFreeHost(c->pin);
   for (auto& e : c->ev_pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
@@ -1122,8 +1128,19 @@ int swcs_pool_gradients_dev(swcs_ctx* c, double* d_g_out, const int64_t* d_subse
     if ((r = ensure(c, c->selbits, ((c->pool_size + 31) / 32) * 4 + 4))) return r;
     CK(launch_k(c, kKOther, [&] { return launch_subset_bits(d_subset, n_subset, (uint32_t*)c->selbits.p, c->pool_size, c->st); }));
     sel = (const uint32_t*)c->selbits.p;
+    const int m = c->n / 2;
+    if (c->opt_screen_scatter && c->kab.p && m <= 32) {  // selected alpha-beta doubles per alpha pair
+      const size_t m2 = (size_t)m * m;
+      if ((r = ensure(c, c->ab_cnt, m2 * 4)) || (r = ensure(c, c->ab_list, m2 * m2 * 8))) return r;
+      CK(launch_k(c, kKOther, [&] {
+        return launch_screen_lists((const int*)c->kab.p, m, sel, (int*)c->ab_cnt.p, (uint2*)c->ab_list.p, c->st);
+      }));
+      c->screen_now = true;
+    }
   }
-  if ((r = sweep(c, g, sel))) return r;
+  r = sweep(c, g, sel);
+  c->screen_now = false;
+  if (r) return r;
   if (d_subset) CK(launch_k(c, kKOther, [&] { return launch_gather_subset(g, d_subset, n_subset, d_g_out, c->st); }));
   return SWCS_OK;
 }
@@ -1404,6 +1421,9 @@ int swcs_set_option(swcs_ctx* c, const char* name, int64_t value) {
   } else if (k == "gate_blocks") {
     if (value < 0) return fail(c, SWCS_ERR_INVALID_ARG, "gate_blocks must be >= 0");
     c->opt_gate_blocks = (int)value;
+  } else if (k == "screen_scatter") {
+    if (value != 0 && value != 1) return fail(c, SWCS_ERR_INVALID_ARG, "screen_scatter must be 0 or 1");
+    c->opt_screen_scatter = (int)value;
   } else if (k == "row_clusters") {
     if (value < 0) return fail(c, SWCS_ERR_INVALID_ARG, "row_clusters must be >= 0");
     c->opt_row_clusters = (int)value;

@@ -150,6 +150,14 @@ struct RowArgs {
   // sharded pool sweep (n_shards > 1): only the target alpha strings of colex rank = shard (mod n_shards),
   // i.e. every E whose alpha string that rank owns; g and acc[0] are then that shard's partial sums
   int shard, n_shards;
+  // screened sweep (screen != 0, with sel_bits): before each target's scatter the row sectors of every
+  // E = A_k D with k selected, and of the state's own determinants, are marked (the cluster's marks
+  // merged); the scatter then forms sigma only in marked sectors, skipping every other pair before its
+  // integral load, and the alpha-beta gather walks, per alpha pair a*m + b, only the selected
+  // (beta pair i*m + j, kab entry) of ab_list[(a*m + b) * m*m ...] (ab_cnt of them)
+  int screen;
+  const int* ab_cnt;
+  const uint2* ab_list;
 };
 
 struct GroupArgs {
@@ -177,6 +185,9 @@ cudaError_t row_sweep_max_clusters(int threads, int occ, int gsz, size_t smem, i
 cudaError_t launch_row_sweep(const RowArgs& a, int threads, int occ, int gsz, int n_clusters, size_t smem,
                              cudaStream_t st);
 cudaError_t launch_group_state(const GroupArgs& g, cudaStream_t st);
+// Selected alpha-beta doubles per alpha pair for the screened sweep (see RowArgs::screen).
+cudaError_t launch_screen_lists(const int* kab, int m, const uint32_t* sel_bits, int* ab_cnt, uint2* ab_list,
+                                cudaStream_t st);
 cudaError_t launch_rbeta(const uint64_t* gkey, const long long* n, const uint32_t* rank_tab, int ks, int nv, int m,
                          int packed, uint32_t* rbeta, cudaStream_t st);
 

@@ -215,9 +215,24 @@ __device__ __forceinline__ int warp_find_entry(const RowEnt* ents, int cnt, uint
   return lo + 31 - __clz(__ballot_sync(0xffffffffu, le));
 }
 
-template <int kRowThreads, bool SCATTER>
+// Passes over a target's pairs: scatter sigma into the row, gather gradients from it, or (screened sweep)
+// mark the row sectors that selected operators will read.
+enum RowPass { kPassScatter = 0, kPassGather = 1, kPassMark = 2 };
+
+__device__ __forceinline__ void mark_sector(unsigned* touched, uint32_t i) {
+  const unsigned bit = sector_bit(i);
+  if (!(touched[sector_word(i)] & bit)) atomicOr(&touched[sector_word(i)], bit);
+}
+
+__device__ __forceinline__ bool selected(const RowArgs& A, int k) {
+  return !A.sel_bits || ((__ldg(&A.sel_bits[k >> 5]) >> (k & 31)) & 1u);
+}
+
+template <int kRowThreads, int PASS>
 __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, double* row, int crank, int gsz,
                           double& e_acc) {
+  constexpr bool SCATTER = PASS == kPassScatter;
+  constexpr bool MARK = PASS == kPassMark;
   constexpr int kRowWarps = kRowThreads / 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m = A.H.n >> 1, ks = A.H.no, nvs = A.H.nv;
@@ -229,7 +244,7 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
   // pair i * m + j in bits 21..30 (rows of at most 2^21 entries)
   const bool packed = A.rbeta_packed != 0;
   const uint32_t rmask = packed ? 0x1FFFFFu : 0x7FFFFFFFu;
-  const bool filt = SCATTER && (A.energy_only || A.n_probe > 0) && dy.touched != nullptr;
+  const bool filt = SCATTER && (A.energy_only || A.n_probe > 0 || A.screen) && dy.touched != nullptr;
   // ---------------- X's own group: diagonal, beta singles, beta-beta doubles; items (determinant, chunk)
   const long long n_items_same = sh.gx_cnt * nch;
   for (long long u = (long long)crank * kRowWarps + warp; u < n_items_same; u += (long long)gsz * kRowWarps) {
@@ -241,7 +256,7 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
     const uint32_t db = even_bits(d >> 1);
     warp_lists(sh, warp, lane, d, m);
     const uint8_t* oa = sh.occ_all[warp];
-    if (ch == 0) {  // diagonal <D|H|D> = sum_i h_ii + 1/2 sum_ij <ij||ij>
+    if (ch == 0 && !MARK) {  // diagonal <D|H|D> = sum_i h_ii + 1/2 sum_ij <ij||ij>
       double hd = 0.0;
       for (int t2 = lane; t2 < A.H.ne; t2 += 32) {
         const int a = oa[t2];
@@ -255,7 +270,7 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
         const uint32_t rd = __ldg(&A.grank[di]);
         if (SCATTER) {
           if (take(touched, filt, rd)) atomicAdd(&row[rd], hd * cd);
-        } else {
+        } else if (!MARK) {
           e_acc += cd * row[rd];
         }
       }
@@ -275,8 +290,10 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
         if (take(touched, filt, re)) atomicAdd(&row[re], apply_sign(fock_single(A, oa, p, r), sb) * cd);
       } else {
         const int k = __ldg(&A.H.ops1[(p < r ? p : r) * A.H.n + (p < r ? r : p)]);
-        if (!A.sel_bits || ((__ldg(&A.sel_bits[k >> 5]) >> (k & 31)) & 1u))
-          atomicAdd(&A.g[k], apply_sign(cd * row[re], sb ^ (int)(p > r)));
+        if (selected(A, k)) {
+          if (MARK) mark_sector(dy.touched, re);
+          else atomicAdd(&A.g[k], apply_sign(cd * row[re], sb ^ (int)(p > r)));
+        }
       }
     }
     // beta-beta doubles, four per lane: every target's loads are issued before the first atomic
@@ -308,7 +325,8 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
           const bool down = pa > pb;
           ix[u] = __ldg(&A.H.opd[down ? (size_t)pb * A.H.npairs + pa : (size_t)pa * A.H.npairs + pb]);
           sg[u] ^= (int)down;
-          if (A.sel_bits && !((__ldg(&A.sel_bits[ix[u] >> 5]) >> (ix[u] & 31)) & 1u)) { ok[u] = false; continue; }
+          if (!selected(A, ix[u])) { ok[u] = false; continue; }
+          if (MARK) { mark_sector(dy.touched, re[u]); ok[u] = false; continue; }
           val[u] = row[re[u]];
         }
       }
@@ -345,8 +363,11 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
       double f = __ldg(&A.H.h[pb * n + pa]);
       for (uint64_t x = d; x; x &= x - 1ull) f += __ldg(&wv[__ffsll((long long)x) - 1]);
       atomicAdd(&row[rd], apply_sign(f, single_phase(d, pa, pb)) * cd);
+    } else if (MARK) {
+      const int k = __ldg(&A.H.ops1[(pa < pb ? pa : pb) * A.H.n + (pa < pb ? pb : pa)]);
+      if (selected(A, k)) mark_sector(dy.touched, rd);
     } else {
-      row_pair<SCATTER>(A, row, touched, filt, __ldg(&A.gkey[di]), __ldg(&A.gamp[di]), rd, pa, -1, pb, -1, nullptr);
+      row_pair<false>(A, row, touched, filt, __ldg(&A.gkey[di]), __ldg(&A.gamp[di]), rd, pa, -1, pb, -1, nullptr);
     }
   }
   // ---------------- alpha-single neighbours, alpha-beta doubles (warp per determinant).
@@ -389,6 +410,30 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
     const int sa = single_phase(d, pa, pb);
     const size_t base = ((size_t)(pa >> 1) * m + (pb >> 1)) * (size_t)m * m;
     const uint32_t* rb = A.rbeta + (size_t)di * nsb;
+    if (!SCATTER && A.screen) {  // screened: only the selected beta pairs (i -> j) of this alpha pair
+      const int ab = (pa >> 1) * m + (pb >> 1);
+      const int cnt = __ldg(&A.ab_cnt[ab]);
+      const uint2* L = A.ab_list + (size_t)ab * m * m;
+      const uint32_t dbs = even_bits(d >> 1);
+      const uint32_t mmask = m >= 32 ? 0xFFFFFFFFu : (1u << m) - 1u;
+      for (int q = lane; q < cnt; q += 32) {
+        const uint2 ent = __ldg(&L[q]);
+        const int i = (int)ent.x / m, j = (int)ent.x - i * m;
+        if (!((dbs >> i) & 1u) || ((dbs >> j) & 1u)) continue;  // i must be occupied, j empty in D
+        // slots of i among D's occupied and of j among its empty beta orbitals: D's beta-single entry
+        const int o = __popc(dbs & ((1u << i) - 1u)), v = __popc(~dbs & mmask & ((1u << j) - 1u));
+        const uint32_t wb = __ldg(&rb[o * nvs + v]);
+        const uint32_t re = wb & rmask;
+        if (MARK) {
+          mark_sector(dy.touched, re);
+        } else {
+          const int kk = (int)ent.y;
+          atomicAdd(&A.g[kk & 0x7FFFFFFF], apply_sign(cd * row[re], (int)(wb >> 31) ^ sa ^ (int)((unsigned)kk >> 31)));
+        }
+      }
+      __syncwarp();
+      continue;
+    }
     for (int t0 = 0; t0 < nsb; t0 += 128) {
       uint32_t wv[4];
       bool ok[4];
@@ -481,13 +526,17 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
       } else {
         const bool down = pa > pb;
         k = __ldg(&A.H.opd[down ? (size_t)pb * npairs + pa : (size_t)pa * npairs + pb]);
-        if (A.sel_bits && !((__ldg(&A.sel_bits[k >> 5]) >> (k & 31)) & 1u)) k = -1;
-        const uint64_t d = __ldg(&A.gkey[di]);
-        const double cd = __ldg(&A.gamp[di]);
-        if (k >= 0) v = apply_sign(cd * row[rd], double_phase(d, p, q, r, s2) ^ (int)down);
+        if (!selected(A, k)) k = -1;
+        if (MARK) {
+          if (k >= 0) mark_sector(dy.touched, rd);
+        } else if (k >= 0) {
+          const uint64_t d = __ldg(&A.gkey[di]);
+          const double cd = __ldg(&A.gamp[di]);
+          v = apply_sign(cd * row[rd], double_phase(d, p, q, r, s2) ^ (int)down);
+        }
       }
     }
-    if (!SCATTER) {
+    if (!SCATTER && !MARK) {
       // segmented sum over the lanes of each entry: lane + o is added while it is in the same entry
       const unsigned later = starts & ~((2u << lane) - 1u);  // starts after this lane
       const int seg_end = later ? __ffs(later) - 1 : 32;
@@ -551,6 +600,7 @@ row_sweep_kernel(RowArgs A) {
   // targets: every alpha string of the sector, in energy-only mode the alpha strings of the state's
   // groups (the others hold no determinant whose sigma is read back), in probe mode the listed ones
   const bool probe = A.n_probe > 0;
+  const bool screen = A.screen && A.sel_bits && dy.touched && !probe && !A.energy_only;
   const int n_targets = probe ? A.n_probe : A.energy_only ? (int)*A.n_groups : A.NA;
   // a shard of the pool sweep visits the alpha strings xi = shard (mod n_shards) only (alpha_list is in
   // colex order, so xi is the string's rank)
@@ -634,10 +684,26 @@ row_sweep_kernel(RowArgs A) {
     scan_items<kRowThreads>(sh, dy.ents_s, sh.n_s, 1, &sh.tot_s);
     scan_items<kRowThreads>(sh, dy.ents_d, sh.n_d, kDblChunk, &sh.tot_d);
 
-    // the other CTA may still be clearing the previous target's sectors: wait for it before scattering
-    // (the clear itself flows straight into this target's discovery)
-    cl.sync();
-    row_phase<kRowThreads, true>(A, sh, dy, row, crank, gsz, e_acc);
+    if (screen) {
+      // the sectors the selected operators read (and the state's own determinants, for the energy),
+      // marked by every CTA for its share of the pairs, then merged over the cluster
+      for (long long t = threadIdx.x; t < sh.gx_cnt; t += kRowThreads) mark_sector(dy.touched, __ldg(&A.grank[sh.gx_off + t]));
+      row_phase<kRowThreads, kPassMark>(A, sh, dy, row, crank, gsz, e_acc);
+      // every CTA's marks are complete and the previous target's sectors cleared
+      cl.sync();
+      for (int w = threadIdx.x; w < nwords; w += kRowThreads) {
+        unsigned bits = 0u;
+        for (int r = 0; r < gsz; ++r)
+          if (r != crank) bits |= cl.map_shared_rank(dy.touched, r)[w];
+        if (bits) atomicOr(&dy.touched[w], bits);
+      }
+      __syncthreads();
+    } else {
+      // the other CTA may still be clearing the previous target's sectors: wait for it before scattering
+      // (the clear itself flows straight into this target's discovery)
+      cl.sync();
+    }
+    row_phase<kRowThreads, kPassScatter>(A, sh, dy, row, crank, gsz, e_acc);
     cl.sync();
     if (probe) {  // the requested entries, split over the cluster
       const int t0 = __ldg(&A.probe_off[xi]), t1 = __ldg(&A.probe_off[xi + 1]);
@@ -651,7 +717,7 @@ row_sweep_kernel(RowArgs A) {
         if (A.sig_out) A.sig_out[A.gorig[di]] = sg;
       }
     } else {
-      row_phase<kRowThreads, false>(A, sh, dy, row, crank, gsz, e_acc);
+      row_phase<kRowThreads, kPassGather>(A, sh, dy, row, crank, gsz, e_acc);
     }
     cl.sync();
     if (dy.touched) {  // clear the entries this CTA touched (others clear theirs)
@@ -797,7 +863,32 @@ __global__ void rbeta_kernel(const uint64_t* gkey, const long long* n_ptr, const
   }
 }
 
+// Per alpha pair (a, b) the selected alpha-beta doubles: (beta pair i*m + j, kab entry) for every
+// (i, j) whose pool operator is selected; one block per alpha pair, order within a pair arbitrary.
+__global__ void screen_lists_kernel(const int* kab, int m, const uint32_t* sel_bits, int* ab_cnt, uint2* ab_list) {
+  __shared__ int cnt;
+  const int ab = blockIdx.x, m2 = m * m;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  for (int ij = threadIdx.x; ij < m2; ij += blockDim.x) {
+    const int kk = kab[(size_t)ab * m2 + ij];
+    if (kk == -1) continue;  // a = b or i = j: no operator
+    const int k = kk & 0x7FFFFFFF;
+    if (!((sel_bits[k >> 5] >> (k & 31)) & 1u)) continue;
+    const int pos = atomicAdd(&cnt, 1);
+    ab_list[(size_t)ab * m2 + pos] = make_uint2((unsigned)ij, (unsigned)kk);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) ab_cnt[ab] = cnt;
+}
+
 }  // namespace
+
+cudaError_t launch_screen_lists(const int* kab, int m, const uint32_t* sel_bits, int* ab_cnt, uint2* ab_list,
+                                cudaStream_t st) {
+  screen_lists_kernel<<<m * m, 256, 0, st>>>(kab, m, sel_bits, ab_cnt, ab_list);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_rbeta(const uint64_t* gkey, const long long* n, const uint32_t* rank_tab, int ks, int nv, int m,
                          int packed, uint32_t* rbeta, cudaStream_t st) {

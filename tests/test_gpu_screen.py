@@ -69,3 +69,49 @@ def test_trained_screen_recalls_argmax(S):
     assert np.mean(recalls) >= 0.75
     assert np.mean(top10) >= 0.5
     net.close()
+
+
+@pytest.mark.parametrize("n_so,n_e,n_ops,seed,n_keep,cluster", [
+    (12, 4, 10, 1, 0, 2), (20, 6, 45, 303, 500, 2), (24, 8, 40, 107, 400, 4), (28, 8, 60, 2, 3000, 1),
+    (28, 8, 60, 2, 3000, 2)])
+@pytest.mark.parametrize("kind", ["top", "random", "alpha_beta", "one"])
+def test_screened_scatter_matches_oracle(S, n_so, n_e, n_ops, seed, n_keep, cluster, kind):
+    """The subset sweep that marks the sectors its operators read and scatters
+    sigma only there: exact on the subset, the energy of the same sweep exact,
+    and equal to the sweep that forms sigma in full."""
+    import torch
+    w = I.small_case(n_so, n_e, n_ops, seed, n_keep=n_keep)
+    c = S.Context()
+    c.load_hamiltonian(w.h, w.g, w.n_so, w.n_e)
+    c.set_option("cluster", cluster)
+    c.apply_ansatz(w.ops, w.theta, n_keep)
+    ko, ao = O.apply_ansatz(w.n_so, w.n_e, w.ops, w.theta, n_keep)
+    go = O.pool_gradients(w.n_so, w.h, w.g, ko, ao)
+    eo, _ = O.energy(w.n_so, w.h, w.g, ko, ao)
+    pool = c.pool_ops()
+    P = len(pool)
+    rng = np.random.default_rng(seed)
+    if kind == "top":
+        sub = np.argsort(-np.abs(go))[:max(1, P // 20)]
+    elif kind == "random":
+        sub = rng.choice(P, max(1, P // 20), replace=False)
+    elif kind == "alpha_beta":  # doubles with one alpha and one beta orbital in each pair
+        ab = np.nonzero((pool[:, 0] == 2) & ((pool[:, 1] % 2) != (pool[:, 2] % 2)))[0]
+        sub = rng.choice(ab, max(1, len(ab) // 20), replace=False)
+    else:
+        sub = np.array([int(np.argmax(np.abs(go)))])
+    sub = np.sort(sub).astype(np.int64)
+    d_sub = torch.from_numpy(sub).cuda()
+    out = {}
+    for scr in (1, 0):
+        c.set_option("screen_scatter", scr)
+        d_g = torch.full((P,), float("nan"), dtype=torch.float64, device="cuda")
+        c.pool_gradients_dev(d_g, d_sub)
+        g = d_g.cpu().numpy()
+        e, _ = c.sweep_energy()
+        assert np.abs(g[sub] - go[sub]).max() < TOL, (scr, np.abs(g[sub] - go[sub]).max())
+        assert np.isnan(np.delete(g, sub)).all()
+        assert abs(e - eo) < TOL
+        out[scr] = g[sub]
+    assert np.abs(out[1] - out[0]).max() < TOL
+    c.close()
