@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -44,7 +45,7 @@ def parse(argv=None):
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="swcs", choices=["swcs", "reference"])
     p.add_argument("--n-keep", type=int, default=1_000_000)
-    p.add_argument("--cpu-sample", type=int, default=400, help="determinants in the oracle's bounded sample")
+    p.add_argument("--cpu-sample", type=int, default=800, help="determinants in the oracle's bounded sample")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--sweep", type=int, default=0, help="0 auto, 1 hashed external table, 2 alpha-string rows")
@@ -126,18 +127,99 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ oracle sample
-def oracle_sample(w, n_sample, n_keep):
-    """Time the oracle's step on the same workload truncated to n_sample
-    determinants; scale by n_keep / n_sample (every part of the oracle's step
-    is linear in the state size at fixed orbitals)."""
+def oracle_sample(w, n_sample):
+    """Wall time of the oracle's step (apply the ansatz truncated to n_sample
+    determinants, energy, full pool gradient) on one host core."""
     import oracle as O
     t0 = time.perf_counter()
     k, a = O.apply_ansatz(w.n_so, w.n_e, w.ops, w.theta, n_sample)
     O.energy(w.n_so, w.h, w.g, k, a)
     O.pool_gradients(w.n_so, w.h, w.g, k, a)
-    dt = time.perf_counter() - t0
-    scale = n_keep / max(len(k), 1)
-    return dt, len(k), 1.0 / (dt * scale)
+    return time.perf_counter() - t0, len(k)
+
+
+def _farm_worker(inq, out, bar, name):
+    sys.path.insert(0, ROOT)
+    import oracle as O  # noqa: F401
+    from paper_2411_07920_gb300 import inputs as I
+    w = I.workload(name)
+    while True:
+        n = inq.get()
+        if n is None:
+            break
+        bar.wait(timeout=900)
+        t0 = time.time()
+        _, nk = oracle_sample(w, n)
+        out.put((t0, time.time(), nk))
+
+
+class OracleFarm:
+    """One single-threaded oracle process per host core (spawned, so they never
+    share a CUDA context), each running the same bounded sample at the same
+    time: the host's whole throughput on the oracle as it stands."""
+
+    def __init__(self, cores, name):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.bar = ctx.Barrier(cores)
+        self.out = ctx.Queue()
+        self.inq = [ctx.Queue() for _ in range(cores)]
+        self.procs = [ctx.Process(target=_farm_worker, args=(q, self.out, self.bar, name), daemon=True)
+                      for q in self.inq]
+        for p in self.procs:
+            p.start()
+
+    def run(self, n_sample):
+        """(wall seconds from the first start to the last finish, determinants per sample)."""
+        for q in self.inq:
+            q.put(n_sample)
+        res = [self.out.get(timeout=1800) for _ in self.inq]
+        return max(r[1] for r in res) - min(r[0] for r in res), res[0][2]
+
+    def close(self):
+        for q in self.inq:
+            q.put(None)
+        for p in self.procs:
+            p.join(timeout=60)
+
+
+def scaling_exponent(n1, t1, n2, t2):
+    return math.log(t2 / t1) / math.log(n2 / n1)
+
+
+def cpu_baseline(w, n_keep, n_small, n_big, configs=True):
+    """The oracle on the machine's host cores: single-threaded at two sample sizes
+    (the fitted exponent carries the time to N), then one process per core on
+    the larger sample at once; plus the two small configurations timed whole."""
+    import oracle as O
+    from paper_2411_07920_gb300 import inputs as I
+    O.build()
+    cores = os.cpu_count() or 1
+    t1, n1 = oracle_sample(w, n_small)
+    t2, n2 = oracle_sample(w, n_big)
+    alpha = scaling_exponent(n1, t1, n2, t2)
+    farm = OracleFarm(cores, WORKLOAD)
+    try:
+        tp, _ = farm.run(n_big)
+    finally:
+        farm.close()
+    sec_per_sweep = tp * (n_keep / n2) ** alpha / cores  # cores sweeps in flight at once
+    res = {"value": 1.0 / sec_per_sweep, "unit": "sweeps/s", "cores": cores, "kind": "oracle",
+           "host_cores": cores,
+           "sample": (f"oracle step (apply 200 gates, energy, full pool gradient) on the same 52/12 workload "
+                      f"truncated to {n2} determinants, run by {cores} single-threaded processes at once "
+                      f"({tp:.1f} s wall); time per sweep carried to N={n_keep} by the exponent {alpha:.3f} "
+                      f"fitted on one core at {n1} ({t1:.1f} s) and {n2} ({t2:.1f} s) determinants"),
+           "single_thread": {"dets": [n1, n2], "s": [round(t1, 3), round(t2, 3)], "exponent": round(alpha, 4)},
+           "parallel": {"processes": cores, "dets": n2, "wall_s": round(tp, 3)}}
+    if configs:
+        out = {}
+        for name in ("so12_e4", "so28_e8"):
+            wc = I.workload(name)
+            t, nk = oracle_sample(wc, wc.n_keep)
+            out[name] = {"dets": nk, "s": round(t, 3), "sweeps_per_s": round(1.0 / t, 6)}
+        res["configs_single_thread"] = out
+    return res
 
 
 def run_reference(args):
@@ -148,25 +230,37 @@ def run_reference(args):
     import oracle as O
     O.build()
     w = I.workload(WORKLOAD, n_keep=args.n_keep)
-    n_sample = min(args.cpu_sample, 100)
-    for _ in range(args.warmup):
-        oracle_sample(w, n_sample, args.n_keep)
-    total = 0.0
-    nk = 0
-    for _ in range(args.steps):
-        dt, nk, _ = oracle_sample(w, n_sample, args.n_keep)
-        total += dt
-    scale = args.n_keep / max(nk, 1)
-    sec_per_sweep = total / args.steps * scale
+    cores = os.cpu_count() or 1
+    n_step = min(args.cpu_sample, 200)
+    farm = OracleFarm(cores, WORKLOAD)
+    try:
+        # the exponent that carries a sample's time to N, from two sample sizes on all cores
+        t_half, n_half = farm.run(max(n_step // 2, 10))
+        for _ in range(args.warmup):
+            t_full, nk = farm.run(n_step)
+        if args.warmup < 1:
+            t_full, nk = farm.run(n_step)
+        alpha = scaling_exponent(n_half, t_half, nk, t_full)
+        total = 0.0
+        for _ in range(args.steps):
+            dt, nk = farm.run(n_step)
+            total += dt
+    finally:
+        farm.close()
+    sec_per_sweep = total / args.steps * (args.n_keep / nk) ** alpha / cores
     value = 1.0 / sec_per_sweep
-    sample = (f"oracle step (apply 200 gates, energy, full pool gradient) on the same 52/12 workload "
-              f"truncated to {nk} determinants, time x {scale:.0f} to N={args.n_keep}")
+    sample = (f"oracle step (apply 200 gates, energy, full pool gradient) on the same 52/12 workload truncated to "
+              f"{nk} determinants, run by {cores} single-threaded processes at once per step "
+              f"({total / args.steps:.2f} s wall per step); time per sweep carried to N={args.n_keep} by the "
+              f"exponent {alpha:.3f} fitted on all cores at {n_half} and {nk} determinants")
     line = {"metric": METRIC, "value": value, "unit": "sweeps/s", "impl": "reference", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_per_sweep * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": "52 spin-orbitals, 12 electrons, 200 gates, N=1e6, "
                                                         "pool 301600 (seed 3)", "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": "sweeps/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "timed_region_s": round(total, 3),
+            "cpu_baseline": {"value": value, "unit": "sweeps/s", "cores": cores, "kind": "oracle", "sample": sample,
+                             "exponent": round(alpha, 4)},
             "e2e": {"value": value, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -337,12 +431,7 @@ def run_swcs(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        import oracle as O
-        O.build()
-        dt, nk, v = oracle_sample(w, args.cpu_sample, args.n_keep)
-        cpu = {"value": v, "unit": "sweeps/s", "cores": 1, "kind": "oracle",
-               "sample": f"oracle step (apply 200 gates, energy, full pool gradient) on the same workload "
-                         f"truncated to {nk} determinants ({dt:.1f} s), scaled x{args.n_keep / nk:.0f} to N={args.n_keep}"}
+        cpu = cpu_baseline(w, args.n_keep, max(args.cpu_sample // 4, 10), args.cpu_sample)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,

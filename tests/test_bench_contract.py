@@ -9,8 +9,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_prints_one_contract_line():
-    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"],
-                         cwd=ROOT, capture_output=True, text=True, timeout=900)
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3",
+                          "--cpu-sample", "40"], cwd=ROOT, capture_output=True, text=True, timeout=900)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.strip().startswith("{")]
     assert len(lines) == 1
@@ -20,7 +20,8 @@ def test_reference_arm_prints_one_contract_line():
         assert k in d, k
     assert d["impl"] == "reference" and d["unit"] == "sweeps/s" and d["higher_is_better"] is True
     assert d["value"] > 0 and d["warmup"] >= 3 and d["steps"] == 1
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == os.cpu_count()
+    assert 0.5 < d["cpu_baseline"]["exponent"] < 2.0  # the fitted growth of the oracle's time with N
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in d["config"]
@@ -38,3 +39,9 @@ def test_committed_traffic_is_reported_only_for_the_captured_launch():
                  ["--rows-l2", "1"], ["--sweep", "1"]):
         assert bench.measured_traffic("row_sweep", bench.parse(argv)) is None, argv
     assert bench.measured_traffic("ansatz", bench.parse([])) is None
+
+
+def test_scaling_exponent_recovers_a_power_law():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert abs(bench.scaling_exponent(100, 2.0, 400, 2.0 * 4 ** 1.25) - 1.25) < 1e-12
