@@ -17,9 +17,10 @@
 // Truncation: entries below the magnitude threshold (or exactly zero) are
 // dropped, then the n_keep largest |c| of the rest are kept, ties at the cut
 // by smaller bitstring.  |c| as an IEEE-754 bit pattern with the sign cleared orders
-// like the value, so an MSD radix select over 8-bit digits (first digit 7
-// bits) finds the cut; when the cut lands on several equal |c| a second
-// radix select over the bitstrings of the tied entries picks the smallest.
+// like the value, so an MSD radix select over 12-bit digits finds the cut (the
+// first digit, the exponent and top mantissa bit, is counted while P1 writes
+// the amplitudes); when the cut lands on several equal |c| a second radix
+// select over the bitstrings of the tied entries picks the smallest.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -30,11 +31,20 @@ namespace swcs {
 
 namespace {
 
-constexpr int kAbsPasses = 8;  // 7 + 7*8 = 63 bits of |c|
-constexpr int kKeyPasses = 8;  // 64 bits of the bitstring
+// Radix select over 12-bit digits.  |c| (63 bits) in digits [51,63) [39,51)
+// [27,39) [15,27) [3,15) [0,3): the first digit is the exponent and the top
+// mantissa bit, so it already splits the amplitudes into 2 bins per binade;
+// the bitstring (64 bits) for exact ties in [52,64) [40,52) ... [0,4).
+constexpr int kBinsLog = 12;
+constexpr int kBins = 1 << kBinsLog;
+constexpr int kAbsPasses = 6;
+constexpr int kKeyPasses = 6;
+constexpr int kPasses = kAbsPasses + kKeyPasses;
 
-__device__ __forceinline__ int abs_shift(int pass) { return 56 - 8 * pass; }
-__device__ __forceinline__ int key_shift(int pass) { return 56 - 8 * pass; }
+__device__ __forceinline__ int abs_hi(int q) { return 63 - kBinsLog * q; }
+__device__ __forceinline__ int abs_lo(int q) { return max(0, 63 - kBinsLog * (q + 1)); }
+__device__ __forceinline__ int key_hi(int q) { return 64 - kBinsLog * q; }
+__device__ __forceinline__ int key_lo(int q) { return max(0, 64 - kBinsLog * (q + 1)); }
 
 __device__ __forceinline__ uint64_t abs_bits(double c) {
   return (uint64_t)__double_as_longlong(c) & 0x7fffffffffffffffull;
@@ -45,10 +55,12 @@ struct SelState {
   unsigned long long prefix;   // |c| bits decided so far
   unsigned long long kprefix;  // bitstring bits decided so far (tie mode)
   long long need;              // rank still to place within the current bucket
-  int shift;                   // digit shift of the last decided |c| digit
-  int kshift;                  // digit shift of the last decided key digit
+  int shift;                   // lowest bit of the last decided |c| digit
+  int kshift;                  // lowest bit of the last decided key digit
   int mode;                    // 0 none (keep all nonzero), 1 cut on |c|, 2 cut on |c| then key
   int pass;                    // passes run
+  int bin;                     // result of the last bin search
+  long long cum, cnt;          // entries before that bin in selection order, entries in it
 };
 
 __device__ __forceinline__ bool keep_entry(const SelState& s, uint64_t key, double c, uint64_t min_bits) {
@@ -58,6 +70,73 @@ __device__ __forceinline__ bool keep_entry(const SelState& s, uint64_t key, doub
   if (s.mode == 1) return (x >> s.shift) >= (s.prefix >> s.shift);
   if (x != s.prefix) return x > s.prefix;
   return (key >> s.kshift) <= (s.kprefix >> s.kshift);
+}
+
+// The bin holding the need-th entry in selection order (descending bins for
+// |c|, ascending for bitstrings) among nb bins of h; the whole block takes
+// part: each thread sums a run of bins, a block scan gives each run's start.
+__device__ void find_bin(const unsigned* h, int nb, long long need, bool desc, SelState& sel, long long* scan) {
+  const int T = blockDim.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int per = (nb + T - 1) / T;
+  const int o0 = min(nb, t * per), o1 = min(nb, o0 + per);
+  long long loc = 0;
+  for (int o = o0; o < o1; ++o) loc += h[desc ? nb - 1 - o : o];
+  long long inc = loc;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const long long v = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += v;
+  }
+  if (lane == 31) scan[wid] = inc;
+  __syncthreads();
+  long long base = 0;
+  for (int w = 0; w < wid; ++w) base += scan[w];
+  long long cum = base + inc - loc;  // entries before this thread's run
+  if (cum < need && cum + loc >= need) {
+    for (int o = o0; o < o1; ++o) {
+      const int v = desc ? nb - 1 - o : o;
+      const long long hv = h[v];
+      if (cum + hv >= need) {
+        sel.bin = v;
+        sel.cum = cum;
+        sel.cnt = hv;
+        break;
+      }
+      cum += hv;
+    }
+  }
+  __syncthreads();
+}
+
+// Index tables of the states inside one launch carry the build's epoch in the
+// high 32 bits of their index word (positions are below 2^32), so a table is
+// never cleared between gates: a slot whose epoch is not the build's reads as
+// empty.  After the last gate the output table is rewritten in the plain form
+// (empty key ~0, index word = position) that every other kernel reads.
+__device__ __forceinline__ bool ep_insert(IdxSlot* t, uint64_t mask, uint64_t key, uint32_t pos, uint32_t ep) {
+  uint64_t s = mix64(key) & mask;
+  const unsigned long long claim = ((unsigned long long)ep << 32) | pos;
+  for (uint64_t n = 0; n <= mask; ++n) {
+    unsigned long long* w = (unsigned long long*)&t[s].idx;
+    const unsigned long long old = ld_key_relaxed((const uint64_t*)w);
+    if ((uint32_t)(old >> 32) != ep && atomicCAS(w, old, claim) == old) {
+      t[s].key = key;
+      return true;
+    }
+    s = (s + 1) & mask;
+  }
+  return false;
+}
+
+__device__ __forceinline__ int64_t ep_lookup(const IdxSlot* __restrict__ t, uint64_t mask, uint64_t key, uint32_t ep) {
+  uint64_t s = mix64(key) & mask;
+  for (uint64_t n = 0; n <= mask; ++n) {
+    const IdxSlot sl = t[s];
+    if ((uint32_t)(sl.idx >> 32) != ep) return -1;  // a slot this build never claimed ends the probe
+    if (sl.key == key) return (int64_t)(uint32_t)sl.idx;
+    s = (s + 1) & mask;
+  }
+  return -1;
 }
 
 // Counters per gate, in a ring of 3 so that the next gate's set can be
@@ -70,7 +149,8 @@ template <int kThreads>
 __global__ void __launch_bounds__(kThreads)
 ansatz_kernel(AnsatzArgs a) {
   __shared__ SelState sel;
-  __shared__ unsigned s_hist[256];
+  __shared__ unsigned s_hist[kBins];
+  __shared__ long long s_scan[32];
   __shared__ long long s_n;
 
   const unsigned nblocks = gridDim.x;
@@ -81,6 +161,7 @@ ansatz_kernel(AnsatzArgs a) {
   uint64_t* keysB = a.keys_b;
   double* ampsB = a.amps_b;
   int tab_cur = a.tab_cur;
+  const size_t hist_set = (size_t)kPasses * kBins;  // two sets, alternating between gates
 
   // ---------------------------------------------------------------- prologue
   if (threadIdx.x == 0) {
@@ -94,15 +175,19 @@ ansatz_kernel(AnsatzArgs a) {
   }
   for (size_t i = gtid; i <= a.tab_mask; i += gstride) {
     a.tab[0][i].key = kEmpty;
+    a.tab[0][i].idx = 0;  // epoch 0: no build
     a.tab[1][i].key = kEmpty;
+    a.tab[1][i].idx = 0;
   }
   for (size_t i = gtid; i < 3 * kCtrN; i += gstride) a.ctr[i] = 0;
+  for (size_t i = gtid; i < hist_set; i += gstride) a.hist[i] = 0;  // the first gate's set
   // test hook: the named CTA leaves without arriving, so every other CTA's
   // bounded wait runs out and the kernel reports kDevTimeout
   if ((int)blockIdx.x == a.skip_arrive_block) return;
   if (!grid_barrier(a.bar, nblocks, a.err, a.timeout_ns)) return;
+  uint32_t ep = 1;  // epoch of the build of tab[tab_cur]
   for (size_t i = gtid; i < (size_t)n; i += gstride) {
-    if (!idx_insert(a.tab[tab_cur], a.tab_mask, keysA[i], i)) set_error(a.err, kDevTableFull);
+    if (!ep_insert(a.tab[tab_cur], a.tab_mask, keysA[i], (uint32_t)i, ep)) set_error(a.err, kDevTableFull);
   }
   if (!grid_barrier(a.bar, nblocks, a.err, a.timeout_ns)) return;
 
@@ -113,11 +198,17 @@ ansatz_kernel(AnsatzArgs a) {
     const double cs = a.cs[2 * g], sn = a.cs[2 * g + 1];
     const IdxSlot* tcur = a.tab[tab_cur];
     IdxSlot* tnxt = a.tab[tab_cur ^ 1];
+    const uint32_t ep_nxt = ep + 1;
+    unsigned* H = a.hist + (size_t)(g & 1) * hist_set;  // this gate's histograms (pass 0 filled below)
 
-    // ------------------------------------------------------------ P1 gate + merge
+    // ------------------------------------------------------------ P1 gate + merge (+ first select digit)
     if (gtid < kCtrN) a.ctr[((g + 1) % 3) * kCtrN + gtid] = 0;
-    for (size_t i = gtid; i < (size_t)(kAbsPasses + kKeyPasses) * 256; i += gstride) a.hist[i] = 0;
-    for (size_t i = gtid; i <= a.tab_mask; i += gstride) tnxt[i].key = kEmpty;
+    {
+      unsigned* Hn = a.hist + (size_t)((g + 1) & 1) * hist_set;  // the next gate's set, last read by gate g-1
+      for (size_t i = gtid; i < hist_set; i += gstride) Hn[i] = 0;
+    }
+    for (int t = threadIdx.x; t < kBins; t += blockDim.x) s_hist[t] = 0;
+    __syncthreads();
     const size_t n_iter = ((size_t)n + gstride - 1) / gstride * gstride;  // warp-converged loop
     for (size_t i = gtid; i < n_iter; i += gstride) {
       const bool live = i < (size_t)n;
@@ -135,7 +226,7 @@ ansatz_kernel(AnsatzArgs a) {
           else sbit = up ? double_phase(d, op.i0, op.i1, op.i2, op.i3) : double_phase(d, op.i2, op.i3, op.i0, op.i1);
           partner = d ^ op.mask_a ^ op.mask_c;
           const double t1 = __dmul_rn(c, cs);
-          const int64_t j = idx_lookup(tcur, a.tab_mask, partner);
+          const int64_t j = ep_lookup(tcur, a.tab_mask, partner, ep);
           if (j >= 0) {
             const double t2 = __dmul_rn(ampsA[j], sn);
             // lower D: c' = c cos - s sin c_U ; upper D: c' = c cos + s sin c_L
@@ -151,6 +242,8 @@ ansatz_kernel(AnsatzArgs a) {
         }
         keysB[i] = d;
         ampsB[i] = out;
+        if (abs_bits(out) >= a.min_abs_bits) atomicAdd(&s_hist[abs_bits(out) >> abs_lo(0)], 1u);
+        if (has_extra) atomicAdd(&s_hist[abs_bits(extra) >> abs_lo(0)], 1u);
       }
       const unsigned long long slot = warp_alloc(&ctr[kCtrExtra], has_extra);
       if (has_extra) {
@@ -166,6 +259,9 @@ ansatz_kernel(AnsatzArgs a) {
       const unsigned zb = __ballot_sync(__activemask(), zero);
       if ((threadIdx.x & 31) == 0 && zb) atomicAdd(&ctr[kCtrZero], (unsigned long long)__popc(zb));
     }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kBins; t += blockDim.x)
+      if (s_hist[t]) atomicAdd(&H[t], s_hist[t]);
     if (!grid_barrier(a.bar, nblocks, a.err, a.timeout_ns)) return;
 
     const long long m = n + (long long)ld_key_relaxed((const uint64_t*)&ctr[kCtrExtra]);
@@ -185,69 +281,60 @@ ansatz_kernel(AnsatzArgs a) {
     __syncthreads();
     if (sel.mode != 0) {
       bool decided = false;
-      for (int p = 0; p < kAbsPasses + kKeyPasses && !decided; ++p) {
+      for (int p = 0; p < kPasses && !decided; ++p) {
         const bool keyphase = p >= kAbsPasses;
-        const int sh = keyphase ? key_shift(p - kAbsPasses) : abs_shift(p);
-        for (int t = threadIdx.x; t < 256; t += blockDim.x) s_hist[t] = 0;
-        __syncthreads();
-        const unsigned long long pre = keyphase ? sel.kprefix : sel.prefix;
-        for (size_t i = gtid; i < (size_t)m; i += gstride) {
-          const double c = ampsB[i];
-          const uint64_t x = abs_bits(c);
-          if (x < a.min_abs_bits) continue;
-          uint64_t v;
-          if (!keyphase) {
-            if (p > 0 && (x >> (sh + 8)) != (pre >> (sh + 8))) continue;
-            v = x;
-          } else {
-            if (x != sel.prefix) continue;
-            const uint64_t k = keysB[i];
-            if (p > kAbsPasses && (k >> (sh + 8)) != (pre >> (sh + 8))) continue;
-            v = k;
+        const int q = keyphase ? p - kAbsPasses : p;
+        const int lo = keyphase ? key_lo(q) : abs_lo(q), hi = keyphase ? key_hi(q) : abs_hi(q);
+        const unsigned dmask = (1u << (hi - lo)) - 1u;
+        unsigned* gh = H + (size_t)p * kBins;
+        if (p > 0) {  // digit 0 of |c| was counted during P1
+          for (int t = threadIdx.x; t < kBins; t += blockDim.x) s_hist[t] = 0;
+          __syncthreads();
+          const unsigned long long pre = keyphase ? sel.kprefix : sel.prefix;
+          for (size_t i = gtid; i < (size_t)m; i += gstride) {
+            const double c = ampsB[i];
+            const uint64_t x = abs_bits(c);
+            if (x < a.min_abs_bits) continue;
+            uint64_t v;
+            if (!keyphase) {
+              if ((x >> hi) != (pre >> hi)) continue;
+              v = x;
+            } else {
+              if (x != sel.prefix) continue;
+              const uint64_t k = keysB[i];
+              if (hi < 64 && (k >> hi) != (pre >> hi)) continue;
+              v = k;
+            }
+            atomicAdd(&s_hist[(v >> lo) & dmask], 1u);
           }
-          atomicAdd(&s_hist[(v >> sh) & 255u], 1u);
+          __syncthreads();
+          for (int t = threadIdx.x; t < kBins; t += blockDim.x)
+            if (s_hist[t]) atomicAdd(&gh[t], s_hist[t]);
+          if (!grid_barrier(a.bar, nblocks, a.err, a.timeout_ns)) return;
         }
+        // the whole block pulls the global bins (past the barrier, from L2) into shared memory
+        for (int t = threadIdx.x; t < kBins; t += blockDim.x) s_hist[t] = __ldcg(&gh[t]);
+        if (threadIdx.x == 0) sel.bin = -1;
         __syncthreads();
-        unsigned* gh = a.hist + p * 256;
-        for (int t = threadIdx.x; t < 256; t += blockDim.x)
-          if (s_hist[t]) atomicAdd(&gh[t], s_hist[t]);
-        if (!grid_barrier(a.bar, nblocks, a.err, a.timeout_ns)) return;
-        // the whole block pulls the 256 global bins (past the barrier, from L2) into shared memory
-        for (int t = threadIdx.x; t < 256; t += blockDim.x) s_hist[t] = __ldcg(&gh[t]);
-        __syncthreads();
+        find_bin(s_hist, (int)dmask + 1, sel.need, !keyphase, sel, s_scan);
         if (threadIdx.x == 0) {
-          long long need = sel.need, cum = 0;
-          int chosen = -1;
-          long long cnt = 0;
-          if (!keyphase) {
-            for (int v = 255; v >= 0; --v) {
-              const long long h = (long long)s_hist[v];
-              if (cum + h >= need) { chosen = v; cnt = h; break; }
-              cum += h;
-            }
-          } else {
-            for (int v = 0; v < 256; ++v) {
-              const long long h = (long long)s_hist[v];
-              if (cum + h >= need) { chosen = v; cnt = h; break; }
-              cum += h;
-            }
-          }
+          int chosen = sel.bin;
           if (chosen < 0) {  // cannot happen: total >= need
             set_error(a.err, kDevBadState);
             chosen = 0;
           }
-          need -= cum;
+          const long long need = sel.need - sel.cum, cnt = sel.cnt;
           sel.need = need;
           sel.pass = p + 1;
           if (!keyphase) {
-            sel.prefix |= (unsigned long long)chosen << sh;
-            sel.shift = sh;
+            sel.prefix |= (unsigned long long)chosen << lo;
+            sel.shift = lo;
             if (cnt == need) decided = true;          // whole bucket kept
-            else if (sh == 0) sel.mode = 2;            // exact |c| ties at the cut
+            else if (lo == 0) sel.mode = 2;            // exact |c| ties at the cut
           } else {
-            sel.kprefix |= (unsigned long long)chosen << sh;
-            sel.kshift = sh;
-            if (cnt == need || sh == 0) decided = true;
+            sel.kprefix |= (unsigned long long)chosen << lo;
+            sel.kshift = lo;
+            if (cnt == need || lo == 0) decided = true;
           }
           if (decided) sel.pass |= 0x100;
         }
@@ -274,7 +361,7 @@ ansatz_kernel(AnsatzArgs a) {
       if (keep) {
         keysA[pos] = k;
         ampsA[pos] = c;
-        if (!idx_insert(tnxt, a.tab_mask, k, pos)) set_error(a.err, kDevTableFull);
+        if (!ep_insert(tnxt, a.tab_mask, k, (uint32_t)pos, ep_nxt)) set_error(a.err, kDevTableFull);
         if (a.snap_keys) {
           a.snap_keys[(size_t)g * a.snap_stride + pos] = k;
           a.snap_amps[(size_t)g * a.snap_stride + pos] = c;
@@ -291,6 +378,20 @@ ansatz_kernel(AnsatzArgs a) {
       atomicAdd((unsigned long long*)&a.stats[7], (unsigned long long)s_gate_in);
     }
     tab_cur ^= 1;
+    ep = ep_nxt;
+  }
+  // the output state's table in the plain form: stale slots empty, index word = position
+  {
+    IdxSlot* t = a.tab[tab_cur];
+    for (size_t i = gtid; i <= a.tab_mask; i += gstride) {
+      const uint64_t w = t[i].idx;
+      if ((uint32_t)(w >> 32) == ep) {
+        t[i].idx = (uint32_t)w;
+      } else {
+        t[i].key = kEmpty;
+        t[i].idx = 0;
+      }
+    }
   }
   if (gtid == 0) {
     *a.n_state = n;

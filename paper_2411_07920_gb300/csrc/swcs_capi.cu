@@ -78,6 +78,7 @@ struct swcs_ctx {
   DevBuf ck_keys, ck_amps, ck_n, sn_keys, sn_amps, sn_n, sigma, nu0, nu1, atab0, atab1, dth;
   DevBuf prb;  // swcs_sigma_at: requested alpha strings, ranges, beta ranks and outputs
   DevBuf ab_cnt, ab_list;  // screened sweep: selected alpha-beta doubles per alpha pair
+  DevBuf selhist;          // gate kernel: radix-select histograms (two sets of 12 passes x 4096 bins)
   int opt_screen_scatter = 1;  // a subset sweep marks and scatters only what the selected operators read
   bool screen_now = false;     // set around a subset sweep whose lists are built
 
@@ -113,7 +114,6 @@ struct Ctrl {
   int err;
   GridBar bar;
   unsigned long long ctr[12];
-  unsigned hist[16 * 256];
   long long stats[8];
   double acc[2];
   double eout[2];
@@ -342,7 +342,7 @@ int ensure_state_buffers(swcs_ctx* c, int64_t max_state) {
     c->cap = cap;
     c->tab_mask = tcap - 1;
   }
-  return SWCS_OK;
+  return ensure(c, c->selhist, kAnsatzHistWords * 4);  // the gate kernel's select histograms
 }
 
 int64_t max_state_for(swcs_ctx* c, int64_t n_keep, int n_ops, int64_t n_now) {
@@ -388,7 +388,8 @@ int run_gates(swcs_ctx* c, const uint8_t* d_ops, const double* d_cs, int n_ops, 
   a.n_state = &k->n_state;
   a.tab_cur_out = &k->tab_cur;
   a.ctr = k->ctr;
-  a.hist = k->hist;
+  if (!c->selhist.p) return fail(c, SWCS_ERR_CUDA, "gate kernel histograms not allocated");
+  a.hist = (unsigned*)c->selhist.p;
   a.bar = &k->bar;
   a.err = &k->err;
   a.timeout_ns = c->opt_timeout_ns;
@@ -770,7 +771,8 @@ int swcs_destroy(swcs_ctx* c) {
                     &c->rbeta, &c->gab, &c->kab, &c->gorig,
                     &c->ck_keys, &c->ck_amps, &c->ck_n, &c->sn_keys, &c->sn_amps, &c->sn_n, &c->sigma, &c->nu0,
                     &c->nu1, &c->atab0, &c->atab1, &c->dth, &c->pool_dev, &c->selbits, &c->feat,
-                    &c->ypred, &c->topk_hist, &c->topk_ctl, &c->occ, &c->prb, &c->ab_cnt, &c->ab_list};
+                    &c->ypred, &c->topk_hist, &c->topk_ctl, &c->occ, &c->prb, &c->ab_cnt, &c->ab_list,
+                    &c->selhist};
   for (DevBuf* b : bufs) release(*b);
   if (c->pin) cudaFreeHost(c->pin);
   for (auto& e : c->ev_pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }

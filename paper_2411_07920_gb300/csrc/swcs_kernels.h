@@ -14,6 +14,7 @@ constexpr int kAnsatzThreads = 1024;        // gate kernel CTA, one state on the
 constexpr int kAnsatzThreadsShared = 256;   // gate kernel CTA, instances sharing the device
 constexpr int kSigmaThreads = 256;
 constexpr int kMaxSpin = 32;  // spin-orbitals of one spin (n_so <= 64)
+constexpr size_t kAnsatzHistWords = 2 * 12 * 4096;  // radix-select histograms of the gate kernel
 
 struct AnsatzArgs {
   uint64_t* keys_a;  // state S (input and output), capacity cap
@@ -34,7 +35,7 @@ struct AnsatzArgs {
   long long* n_state;  // in: input size (unless reset_to_hf); out: output size
   int* tab_cur_out;    // out: which table indexes the output state
   unsigned long long* ctr;  // 12 counters
-  unsigned* hist;           // 16 x 256
+  unsigned* hist;           // kAnsatzHistWords: two sets of 12 passes x 4096 bins
   GridBar* bar;
   int* err;
   uint64_t timeout_ns;
