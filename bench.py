@@ -339,6 +339,22 @@ def run_swcs(args):
     ctx.profile_enable(False)
     ms_per_step, value = aggregate(total_ms, args.steps, world, dev)
 
+    # hash probes of one more (untimed) step: lookups and the index slots they visit, per second of the
+    # kernels that make them (gate kernel: partner lookups of the merge; row sweep: neighbour discovery)
+    ctx.set_option("count_probes", 1)
+    ctx.probe_counts(reset=True)
+    step()
+    pc = ctx.probe_counts(reset=True)
+    ctx.set_option("count_probes", 0)
+    g_ms = prof.get("ansatz", (0.0, 0))[0] / max(args.steps, 1)
+    r_ms = prof.get("row_sweep", (0.0, 0))[0] / max(args.steps, 1)
+    probes = {"gate": {"lookups": pc["gate_lookups"], "slots": pc["gate_slots"],
+                       "slots_per_lookup": round(pc["gate_slots"] / max(pc["gate_lookups"], 1), 4),
+                       "lookups_per_s": pc["gate_lookups"] / (g_ms / 1e3) if g_ms > 0 else None},
+              "row_sweep": {"lookups": pc["row_lookups"], "slots": pc["row_slots"],
+                            "slots_per_lookup": round(pc["row_slots"] / max(pc["row_lookups"], 1), 4),
+                            "lookups_per_s": pc["row_lookups"] / (r_ms / 1e3) if r_ms > 0 else None}}
+
     # ------------------------------------------------------------ roofline of the dominant kernel
     import math
     no, nv = w.n_e // 2, w.n_so // 2 - w.n_e // 2
@@ -441,7 +457,7 @@ def run_swcs(args):
                                        f"N={args.n_keep}, GSD pool {pool}",
                            "parallelism": f"replicas x{world}", "l2": "flushed between steps (512 MB write)"},
                 "gate_dets_per_s": gate_dets_per_s, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clk, "energy_ms": round(min(energy_ms), 3),
+                "gpu_launches": launches, "clocks": clk, "energy_ms": round(min(energy_ms), 3), "hash_probes": probes,
                 "adjoint": adjoint, "batch": batch, "screen": screen_res, "adapt": adapt_res,
                 "kernels_ms": {k: round(v[0], 3) for k, v in prof.items()},
                 "ext": {"distinct": stats["ext_distinct"], "buckets": stats["ext_buckets"],

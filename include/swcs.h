@@ -216,6 +216,13 @@ int swcs_sigma_at(swcs_ctx* ctx, const uint64_t* h_keys, int64_t n, double* h_si
  * largest merged set |Phi|, sum over gates of the input state size
  * (gate x determinant applications)}. */
 int swcs_stats(swcs_ctx* ctx, int64_t* h_out8);
+/* Hash-probe counts accumulated while option "count_probes" is 1 (off by
+ * default; counting adds a few integer operations per lookup):
+ * {partner lookups of the gate kernel (merge of Sec. II.B), index slots they
+ * visited, alpha-string lookups of the row sweep's neighbour discovery, slots
+ * they visited}.  Synchronises; reset != 0 clears them.  The paper has no
+ * counterpart: a measurement of the open-addressing tables. */
+int swcs_probe_counts(swcs_ctx* ctx, int64_t* h_out4, int reset);
 
 /* Tuning options (no effect on results beyond FP64 summation order):
  *   "sweep"    0 automatic (default), 1 hashed external-sigma table,
@@ -237,6 +244,7 @@ int swcs_stats(swcs_ctx* ctx, int64_t* h_out8);
  *              SWCS_ERR_TIMEOUT and the context stays usable
  *   "gate_blocks"   CTAs of the persistent gate kernel (0, default: whole device)
  *   "row_clusters"  clusters of the row sweep (0, default: as many as fit)
+ *   "count_probes"  1: count hash probes (swcs_probe_counts); 0 (default)
  *   "screen_scatter" subset sweeps of swcs_pool_gradients_dev: 1 (default)
  *              scatter sigma only into the sectors the subset reads, 0 form
  *              sigma in full

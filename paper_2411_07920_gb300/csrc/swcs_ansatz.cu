@@ -128,14 +128,22 @@ __device__ __forceinline__ bool ep_insert(IdxSlot* t, uint64_t mask, uint64_t ke
   return false;
 }
 
-__device__ __forceinline__ int64_t ep_lookup(const IdxSlot* __restrict__ t, uint64_t mask, uint64_t key, uint32_t ep) {
+__device__ __forceinline__ int64_t ep_lookup(const IdxSlot* __restrict__ t, uint64_t mask, uint64_t key, uint32_t ep,
+                                             unsigned* probes) {
   uint64_t s = mix64(key) & mask;
   for (uint64_t n = 0; n <= mask; ++n) {
     const IdxSlot sl = t[s];
-    if ((uint32_t)(sl.idx >> 32) != ep) return -1;  // a slot this build never claimed ends the probe
-    if (sl.key == key) return (int64_t)(uint32_t)sl.idx;
+    if ((uint32_t)(sl.idx >> 32) != ep) {  // a slot this build never claimed ends the probe
+      *probes += (unsigned)n + 1u;
+      return -1;
+    }
+    if (sl.key == key) {
+      *probes += (unsigned)n + 1u;
+      return (int64_t)(uint32_t)sl.idx;
+    }
     s = (s + 1) & mask;
   }
+  *probes += (unsigned)(mask + 1);
   return -1;
 }
 
@@ -162,6 +170,7 @@ ansatz_kernel(AnsatzArgs a) {
   double* ampsB = a.amps_b;
   int tab_cur = a.tab_cur;
   const size_t hist_set = (size_t)kPasses * kBins;  // two sets, alternating between gates
+  unsigned n_lookups = 0, n_probe_slots = 0;  // partner lookups and the slots they visited
 
   // ---------------------------------------------------------------- prologue
   if (threadIdx.x == 0) {
@@ -226,7 +235,8 @@ ansatz_kernel(AnsatzArgs a) {
           else sbit = up ? double_phase(d, op.i0, op.i1, op.i2, op.i3) : double_phase(d, op.i2, op.i3, op.i0, op.i1);
           partner = d ^ op.mask_a ^ op.mask_c;
           const double t1 = __dmul_rn(c, cs);
-          const int64_t j = ep_lookup(tcur, a.tab_mask, partner, ep);
+          const int64_t j = ep_lookup(tcur, a.tab_mask, partner, ep, &n_probe_slots);
+          ++n_lookups;
           if (j >= 0) {
             const double t2 = __dmul_rn(ampsA[j], sn);
             // lower D: c' = c cos - s sin c_U ; upper D: c' = c cos + s sin c_L
@@ -392,6 +402,10 @@ ansatz_kernel(AnsatzArgs a) {
         t[i].idx = 0;
       }
     }
+  }
+  if (a.probe_ctr && (n_lookups | n_probe_slots)) {
+    atomicAdd(&a.probe_ctr[0], (unsigned long long)n_lookups);
+    atomicAdd(&a.probe_ctr[1], (unsigned long long)n_probe_slots);
   }
   if (gtid == 0) {
     *a.n_state = n;

@@ -69,6 +69,7 @@ struct swcs_ctx {
   int opt_energy = 0;     // energy: 0 automatic, 1 probe kernel, 2 alpha-string rows
   uint64_t opt_timeout_ns = kTimeoutNs;  // bound of every device-side wait
   int opt_skip_arrive = -1;              // test hook (see swcs_set_option)
+  int opt_count_probes = 0;              // count hash probes of the gate kernel and the row sweep
   uint64_t opt_ext_cap = 0;              // hashed sweep: first table capacity (0: sized from an estimate)
   int opt_gate_blocks = 0;   // CTAs of the gate kernel (0: whole device)
   int opt_gate_threads = kAnsatzThreads;  // threads per gate-kernel CTA (batched instances: kAnsatzThreadsShared)
@@ -119,6 +120,7 @@ struct Ctrl {
   double eout[2];
   unsigned long long n_distinct;
   double ovl[3];  // swcs_overlap: <state|given>, <given|given>, <state|state>
+  unsigned long long probes[4];  // hash probes: gate lookups, their slots, row-sweep lookups, their slots
 };
 
 int fail(swcs_ctx* c, int code, const char* fmt, ...) {
@@ -394,6 +396,7 @@ int run_gates(swcs_ctx* c, const uint8_t* d_ops, const double* d_cs, int n_ops, 
   a.err = &k->err;
   a.timeout_ns = c->opt_timeout_ns;
   a.skip_arrive_block = c->opt_skip_arrive;
+  a.probe_ctr = c->opt_count_probes ? &k->probes[0] : nullptr;
   a.snap_keys = snap_keys;
   a.snap_amps = snap_amps;
   a.snap_n = snap_n;
@@ -611,6 +614,7 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
   ra.n_shards = shard ? shard->n_shards : 1;
   ra.screen = (sel && c->screen_now && twords > 0) ? 1 : 0;
   ra.ab_cnt = (const int*)c->ab_cnt.p;
+  ra.probe_ctr = c->opt_count_probes ? &k->probes[2] : nullptr;
   ra.ab_list = (const uint2*)c->ab_list.p;
   CK(launch_k(c, kKRow, [&] { return launch_row_sweep(ra, nthr, c->opt_row_occ, gsz, ncl, smem, c->st); }));
   c->stats[2] = 0;
@@ -1257,6 +1261,16 @@ int swcs_set_state(swcs_ctx* c, const uint64_t* keys, const double* amps, int64_
   return check_device(c, "swcs_set_state");
 }
 
+int swcs_probe_counts(swcs_ctx* c, int64_t* h_out4, int reset) {
+  if (!c || !h_out4) return SWCS_ERR_INVALID_ARG;
+  unsigned long long v[4];
+  CK(cudaStreamSynchronize(c->st));
+  CK(cudaMemcpy(v, ctrl(c)->probes, sizeof v, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < 4; ++i) h_out4[i] = (int64_t)v[i];
+  if (reset) CK(cudaMemset(ctrl(c)->probes, 0, sizeof v));
+  return SWCS_OK;
+}
+
 int swcs_stats(swcs_ctx* c, int64_t* out8) {
   if (!c || !out8) return SWCS_ERR_INVALID_ARG;
   long long dev[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -1432,6 +1446,9 @@ int swcs_set_option(swcs_ctx* c, const char* name, int64_t value) {
   } else if (k == "wait_timeout_ms") {
     if (value < 1 || value > 60000) return fail(c, SWCS_ERR_INVALID_ARG, "wait_timeout_ms must be 1..60000");
     c->opt_timeout_ns = (uint64_t)value * 1000000ull;
+  } else if (k == "count_probes") {
+    if (value != 0 && value != 1) return fail(c, SWCS_ERR_INVALID_ARG, "count_probes must be 0 or 1");
+    c->opt_count_probes = (int)value;
   } else if (k == "test_skip_arrive") {
     c->opt_skip_arrive = value < 0 ? -1 : (int)value;
   } else if (k == "ext_capacity") {

@@ -55,6 +55,22 @@ __device__ __forceinline__ int64_t idx_lookup(const IdxSlot* __restrict__ t, uin
   return -1;
 }
 
+// The same lookup, also adding the number of slots it visited to *probes.
+__device__ __forceinline__ int64_t idx_lookup_counted(const IdxSlot* __restrict__ t, uint64_t mask, uint64_t key,
+                                                      unsigned* probes) {
+  uint64_t s = mix64(key) & mask;
+  for (uint64_t n = 0; n <= mask; ++n) {
+    const IdxSlot sl = t[s];
+    if (sl.key == key || sl.key == kEmpty) {
+      *probes += (unsigned)n + 1u;
+      return sl.key == key ? (int64_t)sl.idx : -1;
+    }
+    s = (s + 1) & mask;
+  }
+  *probes += (unsigned)(mask + 1);
+  return -1;
+}
+
 // Insert (key -> idx); keys are unique per build.  Returns false when the
 // table has no free slot (cannot happen at load <= 1/2, checked anyway).
 __device__ __forceinline__ bool idx_insert(IdxSlot* t, uint64_t mask, uint64_t key, uint64_t idx) {

@@ -46,6 +46,7 @@ struct AnsatzArgs {
   int64_t snap_stride;
   long long* stats;  // optional: [0] gates, [1] select passes, [6] max |Phi|, [7] sum of input sizes
   int skip_arrive_block;  // test hook: this CTA never arrives at its first grid barrier (-1: off)
+  unsigned long long* probe_ctr;  // optional (nullptr: off): [0] partner lookups, [1] slots they visited
 };
 
 int ansatz_blocks_per_sm(int threads);
@@ -159,6 +160,8 @@ struct RowArgs {
   int screen;
   const int* ab_cnt;
   const uint2* ab_list;
+  // optional hash-probe counters (nullptr: off): [0] alpha-string lookups, [1] slots they visited
+  unsigned long long* probe_ctr;
 };
 
 struct GroupArgs {

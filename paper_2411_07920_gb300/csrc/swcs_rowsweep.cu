@@ -595,6 +595,7 @@ row_sweep_kernel(RowArgs A) {
     dy.same_tab[t] = code;
   }
   double e_acc = 0.0;
+  unsigned n_lookups = 0, n_probe_slots = 0;  // hash-probe counters (when requested)
   __syncthreads();
 
   // targets: every alpha string of the sector, in energy-only mode the alpha strings of the state's
@@ -659,7 +660,13 @@ row_sweep_kernel(RowArgs A) {
         Y = X ^ (1u << b1) ^ (1u << b2) ^ (1u << a1) ^ (1u << a2);
         o4[0] = (uint8_t)(2 * a1); o4[1] = (uint8_t)(2 * a2); o4[2] = (uint8_t)(2 * b1); o4[3] = (uint8_t)(2 * b2);
       }
-      const int64_t g = idx_lookup(A.atab, A.amask, (uint64_t)Y);
+      int64_t g;
+      if (A.probe_ctr) {
+        g = idx_lookup_counted(A.atab, A.amask, (uint64_t)Y, &n_probe_slots);
+        ++n_lookups;
+      } else {
+        g = idx_lookup(A.atab, A.amask, (uint64_t)Y);
+      }
       if (g >= 0) {
         RowEnt en;
         en.off = (uint32_t)A.goff[g];
@@ -742,6 +749,10 @@ row_sweep_kernel(RowArgs A) {
       const int64_t b = per * crank, e = (A.NB < b + per) ? A.NB : b + per;
       for (int64_t i = b + threadIdx.x; i < e; i += kRowThreads) row[i] = 0.0;
     }
+  }
+  if (A.probe_ctr && (n_lookups | n_probe_slots)) {
+    atomicAdd(&A.probe_ctr[0], (unsigned long long)n_lookups);
+    atomicAdd(&A.probe_ctr[1], (unsigned long long)n_probe_slots);
   }
   // energy numerator
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -89,6 +89,7 @@ _SIGS = {
     "swcs_get_sigma": ([_vp, _vp, _vp, _i64, _p64], _i),
     "swcs_sigma_at": ([_vp, _vp, _i64, _vp], _i),
     "swcs_pool_gradients_partial_dev": ([_vp, _i, _i, _vp, _vp], _i),
+    "swcs_probe_counts": ([_vp, _vp, _i], _i),
     "swcs_pool_screen_dev": ([_vp, _vp, ctypes.c_double, _vp, _p64], _i),
 }
 
@@ -396,6 +397,13 @@ class Context:
     def pool_gradients_dev(self, d_g, d_subset=None):
         n = 0 if d_subset is None else int(d_subset.numel())
         self._ck(lib.swcs_pool_gradients_dev(self._h, _tptr(d_g), _tptr(d_subset), n))
+
+    def probe_counts(self, reset=False):
+        """Hash-probe counts while option count_probes is on: {gate lookups, their slots,
+        row-sweep alpha-string lookups, their slots}."""
+        out = np.zeros(4, np.int64)
+        self._ck(lib.swcs_probe_counts(self._h, _ptr(out), int(bool(reset))))
+        return dict(gate_lookups=int(out[0]), gate_slots=int(out[1]), row_lookups=int(out[2]), row_slots=int(out[3]))
 
     def pool_gradients_partial_dev(self, shard, n_shards, d_graw, d_acc):
         """One shard of the pool sweep: unscaled partial gradient into d_graw and
