@@ -339,33 +339,53 @@ int swcs_pool_features_dev(swcs_ctx* ctx, uint16_t* d_x);
 int swcs_pool_screen_dev(swcs_ctx* ctx, swcs_mlp* m, double frac, int64_t* d_subset, int64_t* h_n_subset);
 
 /* Batched launch: many independent instances (each its own Hamiltonian,
- * ansatz and N_keep) evaluated together -- ansatz, energy and full pool
- * gradient -- by one CUDA graph launch.  Each instance's pipeline (persistent
- * gate kernel, alpha-string grouping, row sweep, finalisation) runs on its own
- * branch of the graph with a share of the device proportional to its work.
+ * ansatz and N_keep) evaluated together -- ansatz with truncation after every
+ * gate (Eq. 1, Sec. II.B), energy and full pool gradient (Sec. II.C) -- by one
+ * launch.  By default (mode 0) that launch is one persistent kernel: every
+ * instance walks a chain of phases (index tables; per gate the gate pass, the
+ * select passes it needs and the compaction; grouping by alpha string;
+ * beta-single tables; the row sweep, one target alpha string per tile;
+ * finish), each phase is split into tiles, and the kernel's CTAs take
+ * (instance, phase, tile) work items from per-instance atomic words; the CTA
+ * that finishes a phase's last tile runs its epilogue and publishes the next
+ * phase.  Waits for work are bounded (SWCS_ERR_TIMEOUT).  The launch is
+ * captured in a CUDA graph together with the reset of its scheduler words.
+ * Mode 1 instead captures each instance's own kernels on a branch of a graph.
  *   swcs_batch_add     copies the inputs (same meaning as swcs_load_hamiltonian
  *                      and swcs_apply_ansatz); *index_out = instance index
+ *   swcs_batch_set_tuning  mode (0 persistent, 1 graph branches), items per
+ *                      tile (256..2^20), CTAs per SM (1 or 2) and the
+ *                      alpha-string table's capacity factor (2, 4 or 8 times
+ *                      the state bound) used by the next non-autotuned build
  *   swcs_batch_build   sizes every buffer and captures the graph; autotune != 0
- *                      first times candidate device shares and row-sweep
- *                      cluster sizes on the whole graph and keeps the fastest
+ *                      first times candidate settings on whole launches and
+ *                      keeps the fastest (mode 0: tile x CTAs per SM x table
+ *                      factor; mode 1: device shares x row-sweep cluster sizes)
  *   swcs_batch_run     one cudaGraphLaunch on the stream given at creation (when
  *                      that is NULL, on a blocking stream owned by the batch)
+ *   swcs_batch_run_serial  the library's own per-instance kernels for every
+ *                      instance back to back on that stream (no graph, no
+ *                      synchronisation between instances): the comparator
  *   swcs_batch_results synchronises; E, <psi|psi> and the pool gradient
  *                      (swcs_batch_pool_size entries) of instance i
- *   swcs_batch_tuning  {device share, cluster size, tuned graph ms, instances}
- * Instances whose beta-string space exceeds 2^22 are rejected at build. */
+ *   swcs_batch_tuning  {mode, tile, CTAs per SM, table factor, tuned ms,
+ *                      instances, device share, cluster size}
+ * Instances whose beta-string space exceeds 2^22 are rejected at build.  The
+ * paper has no batched launch: this is a throughput service of the library. */
 typedef struct swcs_batch swcs_batch;
 int swcs_batch_create(swcs_batch** out, void* cuda_stream);
 int swcs_batch_destroy(swcs_batch* b);
 const char* swcs_batch_last_error(const swcs_batch* b);
 int swcs_batch_add(swcs_batch* b, const double* h_h, const double* h_g, int n_so, int n_elec, const uint8_t* h_ops,
                    const double* h_theta, int n_ops, int64_t n_keep, int* index_out);
+int swcs_batch_set_tuning(swcs_batch* b, int mode, int tile, int ctas_per_sm, int hash_factor);
 int swcs_batch_build(swcs_batch* b, int autotune);
 int swcs_batch_run(swcs_batch* b);
+int swcs_batch_run_serial(swcs_batch* b);
 int swcs_batch_size(swcs_batch* b, int* n_out);
 int swcs_batch_pool_size(swcs_batch* b, int i, int64_t* n_out);
 int swcs_batch_results(swcs_batch* b, int i, double* h_e, double* h_norm2, double* h_g);
-int swcs_batch_tuning(swcs_batch* b, double* h_out4);
+int swcs_batch_tuning(swcs_batch* b, double* h_out8);
 
 #ifdef __cplusplus
 }

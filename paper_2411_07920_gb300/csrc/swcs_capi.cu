@@ -359,12 +359,9 @@ int64_t max_state_for(swcs_ctx* c, int64_t n_keep, int n_ops, int64_t n_now) {
 // in the kept set (ranked below every nonzero |c|) unless a criterion cuts
 // them -- the projectors of the adjoint need them (a partner at theta = 0 has
 // c = 0 but a nonzero derivative); the magnitude criterion still drops them.
-int run_gates(swcs_ctx* c, const uint8_t* d_ops, const double* d_cs, int n_ops, int64_t n_keep, bool reset,
-              uint64_t* snap_keys = nullptr, double* snap_amps = nullptr, long long* snap_n = nullptr,
-              int64_t snap_stride = 0, bool keep_zeros = false) {
-  const int gthreads = c->opt_gate_threads;
-  const int bps = ansatz_blocks_per_sm(gthreads);
-  if (bps <= 0) return fail(c, SWCS_ERR_NO_DEVICE, "ansatz kernel cannot be resident on this device");
+// The gate kernel's arguments for this context (no launch).
+AnsatzArgs gate_args(swcs_ctx* c, const uint8_t* d_ops, const double* d_cs, int n_ops, int64_t n_keep, bool reset,
+                     uint64_t* snap_keys, double* snap_amps, long long* snap_n, int64_t snap_stride, bool keep_zeros) {
   AnsatzArgs a{};
   a.keys_a = (uint64_t*)c->keys_a.p;
   a.amps_a = (double*)c->amps_a.p;
@@ -390,7 +387,6 @@ int run_gates(swcs_ctx* c, const uint8_t* d_ops, const double* d_cs, int n_ops, 
   a.n_state = &k->n_state;
   a.tab_cur_out = &k->tab_cur;
   a.ctr = k->ctr;
-  if (!c->selhist.p) return fail(c, SWCS_ERR_CUDA, "gate kernel histograms not allocated");
   a.hist = (unsigned*)c->selhist.p;
   a.bar = &k->bar;
   a.err = &k->err;
@@ -402,6 +398,19 @@ int run_gates(swcs_ctx* c, const uint8_t* d_ops, const double* d_cs, int n_ops, 
   a.snap_n = snap_n;
   a.snap_stride = snap_stride;
   a.stats = k->stats;
+  return a;
+}
+
+int run_gates(swcs_ctx* c, const uint8_t* d_ops, const double* d_cs, int n_ops, int64_t n_keep, bool reset,
+              uint64_t* snap_keys = nullptr, double* snap_amps = nullptr, long long* snap_n = nullptr,
+              int64_t snap_stride = 0, bool keep_zeros = false) {
+  const int gthreads = c->opt_gate_threads;
+  const int bps = ansatz_blocks_per_sm(gthreads);
+  if (bps <= 0) return fail(c, SWCS_ERR_NO_DEVICE, "ansatz kernel cannot be resident on this device");
+  if (!c->selhist.p) return fail(c, SWCS_ERR_CUDA, "gate kernel histograms not allocated");
+  const AnsatzArgs a = gate_args(c, d_ops, d_cs, n_ops, n_keep, reset, snap_keys, snap_amps, snap_n, snap_stride,
+                                 keep_zeros);
+  Ctrl* k = ctrl(c);
   // barrier words must start at zero
   CK(cudaMemsetAsync(&k->bar, 0, sizeof(GridBar), c->st));
   int nblocks = c->nsm * bps;
@@ -495,6 +504,64 @@ struct RowProbe {
   double* out = nullptr;
 };
 
+// Arguments of the grouping kernels and of the row sweep for this context's
+// buffers (alpha-string table of capacity acap); the caller sets the mode fields.
+GroupArgs group_args(swcs_ctx* c, uint64_t acap) {
+  Ctrl* k = ctrl(c);
+  GroupArgs ga{};
+  ga.keys = (const uint64_t*)c->keys_a.p;
+  ga.amps = (const double*)c->amps_a.p;
+  ga.n = &k->n_state;
+  ga.atab = (IdxSlot*)c->atab.p;
+  ga.amask = acap - 1;
+  ga.n_groups = &k->n_distinct;
+  ga.gid_of = (uint32_t*)c->gid_of.p;
+  ga.gcount = (long long*)c->gcount.p;
+  ga.goff = (long long*)c->goff.p;
+  ga.gfill = (long long*)c->gfill.p;
+  ga.gkey = (uint64_t*)c->gkey.p;
+  ga.gamp = (double*)c->gamp.p;
+  ga.grank = (uint32_t*)c->grank.p;
+  ga.gorig = (uint32_t*)c->gorig.p;
+  ga.rank_tab = (const uint32_t*)c->rank_tab.p;
+  ga.ks = c->no;
+  ga.acc = k->acc;
+  return ga;
+}
+
+RowArgs row_args(swcs_ctx* c, const GroupArgs& ga, double* d_g, int max_s, int max_d, int twords, int rbeta_packed) {
+  Ctrl* k = ctrl(c);
+  RowArgs ra{};
+  ra.H = ham_dev(c);
+  ra.gkey = ga.gkey;
+  ra.gamp = ga.gamp;
+  ra.grank = ga.grank;
+  ra.goff = ga.goff;
+  ra.atab = ga.atab;
+  ra.amask = ga.amask;
+  ra.alpha_list = (const uint32_t*)c->alpha_list.p;
+  ra.NA = c->NA;
+  ra.rank_tab = ga.rank_tab;
+  ra.rows = (double*)c->rows.p;
+  ra.NB = c->NB;
+  ra.g = d_g;
+  ra.acc = k->acc;
+  ra.err = &k->err;
+  ra.max_ent_s = max_s;
+  ra.max_ent_d = max_d;
+  ra.touched_words = twords;
+  ra.rbeta = (const uint32_t*)c->rbeta.p;
+  ra.rbeta_packed = rbeta_packed;
+  ra.gab = (const double*)c->gab.p;
+  ra.kab = (const int*)c->kab.p;
+  ra.gorig = (const uint32_t*)c->gorig.p;
+  ra.n_groups = ga.n_groups;
+  ra.n_shards = 1;
+  ra.ab_cnt = (const int*)c->ab_cnt.p;
+  ra.ab_list = (const uint2*)c->ab_list.p;
+  return ra;
+}
+
 // A shard of the pool sweep (swcs_pool_gradients_partial_dev): target alpha strings of colex rank
 // shard (mod n_shards); the gradient is left unscaled and the energy unfinished.
 struct RowShard {
@@ -552,24 +619,7 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
   CK(cudaMemsetAsync(k->acc, 0, 16, c->st));
   if (!energy_only && !probe) CK(cudaMemsetAsync(d_g, 0, sizeof(double) * c->pool_size, c->st));
   CK(cudaMemsetAsync(c->rows.p, 0, (size_t)ncl * ((c->NB + 3) & ~(int64_t)3) * 8, c->st));  // rows padded to 32 B
-  GroupArgs ga;
-  ga.keys = (const uint64_t*)c->keys_a.p;
-  ga.amps = (const double*)c->amps_a.p;
-  ga.n = &k->n_state;
-  ga.atab = (IdxSlot*)c->atab.p;
-  ga.amask = acap - 1;
-  ga.n_groups = &k->n_distinct;
-  ga.gid_of = (uint32_t*)c->gid_of.p;
-  ga.gcount = (long long*)c->gcount.p;
-  ga.goff = (long long*)c->goff.p;
-  ga.gfill = (long long*)c->gfill.p;
-  ga.gkey = (uint64_t*)c->gkey.p;
-  ga.gamp = (double*)c->gamp.p;
-  ga.grank = (uint32_t*)c->grank.p;
-  ga.gorig = (uint32_t*)c->gorig.p;
-  ga.rank_tab = (const uint32_t*)c->rank_tab.p;
-  ga.ks = ks;
-  ga.acc = k->acc;
+  const GroupArgs ga = group_args(c, acap);
   CK(launch_k(c, kKGroup, [&] { return launch_group_state(ga, c->st); }));
   c->launches += 4;  // five grouping kernels in one call
   // beta-single entries carry the spatial pair i * m + j too when ranks fit 21 bits and pairs 10
@@ -577,34 +627,10 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
   CK(launch_k(c, kKGroup, [&] {
     return launch_rbeta(ga.gkey, ga.n, ga.rank_tab, ks, nvs, m, rbeta_packed, (uint32_t*)c->rbeta.p, c->st);
   }));
-  RowArgs ra;
-  ra.H = ham_dev(c);
-  ra.gkey = ga.gkey;
-  ra.gamp = ga.gamp;
-  ra.grank = ga.grank;
-  ra.goff = ga.goff;
-  ra.atab = ga.atab;
-  ra.amask = ga.amask;
-  ra.alpha_list = (const uint32_t*)c->alpha_list.p;
-  ra.NA = c->NA;
-  ra.rank_tab = ga.rank_tab;
-  ra.rows = (double*)c->rows.p;
-  ra.NB = c->NB;
-  ra.g = d_g;
-  ra.acc = k->acc;
-  ra.err = &k->err;
-  ra.max_ent_s = max_s;
-  ra.max_ent_d = max_d;
-  ra.touched_words = twords;
+  RowArgs ra = row_args(c, ga, d_g, max_s, max_d, twords, rbeta_packed);
   ra.sel_bits = sel;
-  ra.rbeta = (const uint32_t*)c->rbeta.p;
-  ra.rbeta_packed = rbeta_packed;
-  ra.gab = (const double*)c->gab.p;
-  ra.kab = (const int*)c->kab.p;
   ra.energy_only = energy_only ? 1 : 0;
   ra.sig_out = sig_out;
-  ra.gorig = (const uint32_t*)c->gorig.p;
-  ra.n_groups = ga.n_groups;
   ra.n_probe = probe ? probe->n : 0;
   ra.probe_x = probe ? probe->x : nullptr;
   ra.probe_off = probe ? probe->off : nullptr;
@@ -613,9 +639,7 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
   ra.shard = shard ? shard->shard : 0;
   ra.n_shards = shard ? shard->n_shards : 1;
   ra.screen = (sel && c->screen_now && twords > 0) ? 1 : 0;
-  ra.ab_cnt = (const int*)c->ab_cnt.p;
   ra.probe_ctr = c->opt_count_probes ? &k->probes[2] : nullptr;
-  ra.ab_list = (const uint2*)c->ab_list.p;
   CK(launch_k(c, kKRow, [&] { return launch_row_sweep(ra, nthr, c->opt_row_occ, gsz, ncl, smem, c->st); }));
   c->stats[2] = 0;
   c->stats[3] = ncl;
@@ -1667,6 +1691,16 @@ struct swcs_batch {
   double share = 1.0;
   int cluster = 2;
   float tuned_ms = 0.f;
+  // persistent launch (mode 0, default) and its tuning; mode 1 is the graph of per-instance stream branches
+  int mode = 0;
+  int tile = 4096, occ = 2, hash_factor = 2;
+  void* d_inst = nullptr;
+  BatchSched* d_sched = nullptr;
+  BatchSched* d_sched0 = nullptr;  // the initial scheduler state, copied in before every launch
+  double* d_rows = nullptr;
+  int* d_status = nullptr;
+  size_t rows_bytes = 0, inst_bytes = 0;
+  int nblocks = 0;
 };
 
 namespace {
@@ -1738,12 +1772,135 @@ int batch_capture(swcs_batch* b, double share, int cluster) {
   e = cudaGraphInstantiate(&b->exec, g, 0);
   if (e != cudaSuccess) return bfail(b, SWCS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   for (int i = 0; i < n; ++i) b->inst[i]->have_state = true;
+  b->mode = 1;
+  return SWCS_OK;
+}
+
+void batch_free_persistent(swcs_batch* b) {
+  for (void* p : {(void*)b->d_inst, (void*)b->d_sched, (void*)b->d_sched0, (void*)b->d_rows, (void*)b->d_status})
+    if (p) cudaFree(p);
+  b->d_inst = nullptr;
+  b->d_sched = b->d_sched0 = nullptr;
+  b->d_rows = nullptr;
+  b->d_status = nullptr;
+  b->rows_bytes = b->inst_bytes = 0;
+}
+
+// The persistent launch: per-instance descriptors (gate, grouping and row-sweep
+// arguments over the instance's own buffers), the initial scheduler words, and
+// a graph of {scheduler reset, status reset, row reset, the kernel}.
+int batch_build_persistent(swcs_batch* b, int tile, int occ, int hash_factor) {
+  batch_drop_graph(b);
+  const int n = (int)b->inst.size();
+  std::vector<BatchInst> hi(n);
+  std::vector<BatchSched> hs(n);
+  size_t dyn = 0;
+  int64_t max_nb = 4;
+  for (int i = 0; i < n; ++i) {
+    swcs_ctx* c = b->inst[i];
+    const int m = c->n / 2;
+    if (m > 32 || c->NB <= 0 || c->NB > (1 << 22)) return bfail(b, SWCS_ERR_INVALID_ARG, "batch: an instance's sector does not fit the row sweep");
+    const int64_t nd = b->max_state[i];
+    const int ks = c->no, nvs = c->nv;
+    const int ns = ks * nvs, ndb = (ks * (ks - 1) / 2) * (nvs * (nvs - 1) / 2);
+    const int max_s = ns + 1, max_d = ndb + 1, t_same = 1 + ns + ndb;  // one CTA per target: all its entries
+    int twords = (int)((c->NB + 127) / 128);
+    size_t smem = row_sweep_smem(max_s, max_d, t_same, twords);
+    if (smem > 96 * 1024) {
+      twords = 0;
+      smem = row_sweep_smem(max_s, max_d, t_same, 0);
+    }
+    if (smem > 96 * 1024) return bfail(b, SWCS_ERR_INVALID_ARG, "batch: an instance's sector does not fit the row sweep");
+    dyn = std::max(dyn, smem);
+    max_nb = std::max<int64_t>(max_nb, c->NB);
+    const uint64_t acap = pow2_at_least((uint64_t)std::max<int64_t>((int64_t)hash_factor * nd, 64));
+    int r;
+    if ((r = ensure(c, c->atab, acap * sizeof(IdxSlot))) || (r = ensure(c, c->gid_of, nd * 4 + 4)) ||
+        (r = ensure(c, c->gcount, nd * 8 + 8)) || (r = ensure(c, c->goff, nd * 8 + 16)) ||
+        (r = ensure(c, c->gfill, nd * 8 + 8)) || (r = ensure(c, c->gkey, nd * 8 + 8)) ||
+        (r = ensure(c, c->gamp, nd * 8 + 8)) || (r = ensure(c, c->grank, nd * 4 + 4)) ||
+        (r = ensure(c, c->rbeta, (size_t)std::max<int64_t>(nd, 1) * ks * nvs * 4)) ||
+        (r = ensure(c, c->gorig, (size_t)std::max<int64_t>(nd, 1) * 4)))
+      return bfail(b, r, "batch: " + c->err);
+    const int packed = c->NB <= (1 << 21) && m <= 32 ? 1 : 0;
+    BatchInst& I = hi[i];
+    I.ga = gate_args(c, (const uint8_t*)c->ops_dev.p, (const double*)c->cs_dev.p, b->n_ops[i], b->n_keep[i], true,
+                     nullptr, nullptr, nullptr, 0, false);
+    I.gr = group_args(c, acap);
+    I.ra = row_args(c, I.gr, (double*)c->gdev.p, max_s, max_d, twords, packed);
+    I.n_ops = b->n_ops[i];
+    I.tile = tile;
+    I.ks = ks;
+    I.nvs = nvs;
+    I.m = m;
+    I.packed = packed;
+    I.acap = acap;
+    I.g = (double*)c->gdev.p;
+    I.pool_size = c->pool_size;
+    I.eout = ctrl(c)->eout;
+    BatchSched& S = hs[i];
+    S = BatchSched{};
+    S.tab_cur = 0;
+    S.ep = 1;
+    S.slot[0].phase = 0;
+    S.slot[0].type = kPhInit;
+    S.slot[0].ntiles = (unsigned)((c->tab_mask + 1 + tile - 1) / tile);
+    S.slot[1].phase = 0xFFFFFFFFu;
+    S.slot[1].type = kPhDone;
+  }
+  const int bps = std::min(occ, batch_blocks_per_sm(dyn));
+  if (bps <= 0) return bfail(b, SWCS_ERR_NO_DEVICE, "batch: the persistent kernel cannot be resident on this device");
+  const int nblocks = b->inst[0]->nsm * bps;
+  const int64_t row_stride = (max_nb + 3) & ~(int64_t)3;
+  const size_t rows_bytes = (size_t)nblocks * row_stride * 8;
+  batch_free_persistent(b);
+  if (cudaMalloc(&b->d_inst, n * sizeof(BatchInst)) != cudaSuccess ||
+      cudaMalloc((void**)&b->d_sched, n * sizeof(BatchSched)) != cudaSuccess ||
+      cudaMalloc((void**)&b->d_sched0, n * sizeof(BatchSched)) != cudaSuccess ||
+      cudaMalloc((void**)&b->d_rows, rows_bytes) != cudaSuccess || cudaMalloc((void**)&b->d_status, 16) != cudaSuccess) {
+    batch_free_persistent(b);
+    return bfail(b, SWCS_ERR_OOM, "batch: device memory for the persistent launch");
+  }
+  b->rows_bytes = rows_bytes;
+  b->nblocks = nblocks;
+  if (cudaMemcpy(b->d_inst, hi.data(), n * sizeof(BatchInst), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_sched0, hs.data(), n * sizeof(BatchSched), cudaMemcpyHostToDevice) != cudaSuccess)
+    return bfail(b, SWCS_ERR_CUDA, "batch: descriptor upload failed");
+  const uint64_t timeout = b->inst[0]->opt_timeout_ns;
+  cudaError_t e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return bfail(b, SWCS_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+  cudaMemcpyAsync(b->d_sched, b->d_sched0, n * sizeof(BatchSched), cudaMemcpyDeviceToDevice, b->origin);
+  cudaMemsetAsync(b->d_status, 0, 16, b->origin);
+  cudaMemsetAsync(b->d_rows, 0, rows_bytes, b->origin);
+  e = launch_batch((const BatchInst*)b->d_inst, b->d_sched, n, b->d_rows, row_stride, b->d_status, nblocks, dyn, timeout,
+                   b->origin);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(b->origin, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return bfail(b, SWCS_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  b->graph = g;
+  e = cudaGraphInstantiate(&b->exec, g, 0);
+  if (e != cudaSuccess) return bfail(b, SWCS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  b->tile = tile;
+  b->occ = occ;
+  b->hash_factor = hash_factor;
+  b->mode = 0;
+  for (int i = 0; i < n; ++i) b->inst[i]->have_state = false;  // the index tables stay in the launch's internal form
   return SWCS_OK;
 }
 
 int batch_check(swcs_batch* b) {
   cudaError_t e = cudaStreamSynchronize(b->origin);
   if (e != cudaSuccess) return bfail(b, SWCS_ERR_CUDA, std::string("batch run: ") + cudaGetErrorString(e));
+  if (b->mode == 0 && b->d_status) {
+    int st[2] = {0, 0};
+    if (cudaMemcpy(st, b->d_status, 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return bfail(b, SWCS_ERR_CUDA, "batch run: status read failed");
+    if (st[1] != 0) return bfail(b, SWCS_ERR_TIMEOUT, "batch run: a bounded wait for work ran out");
+    if (st[0] != (int)b->inst.size()) return bfail(b, SWCS_ERR_CUDA, "batch run: not every instance finished");
+  }
   for (swcs_ctx* c : b->inst) {
     int r = check_device(c, "batch instance");
     if (r) return bfail(b, r, c->err);
@@ -1777,6 +1934,7 @@ int swcs_batch_destroy(swcs_batch* b) {
   if (!b) return SWCS_OK;
   cudaStreamSynchronize(b->origin);
   batch_drop_graph(b);
+  batch_free_persistent(b);
   for (swcs_ctx* c : b->inst) swcs_destroy(c);
   for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
   for (cudaEvent_t e : b->done) cudaEventDestroy(e);
@@ -1828,8 +1986,61 @@ int swcs_batch_add(swcs_batch* b, const double* h_h, const double* h_g, int n_so
   return SWCS_OK;
 }
 
+int swcs_batch_set_tuning(swcs_batch* b, int mode, int tile, int ctas_per_sm, int hash_factor) {
+  if (!b) return SWCS_ERR_INVALID_ARG;
+  if ((mode != 0 && mode != 1) || tile < 256 || tile > (1 << 20) || ctas_per_sm < 1 || ctas_per_sm > 2 ||
+      (hash_factor != 2 && hash_factor != 4 && hash_factor != 8))
+    return bfail(b, SWCS_ERR_INVALID_ARG, "batch_set_tuning: mode 0|1, tile 256..2^20, ctas_per_sm 1|2, hash_factor 2|4|8");
+  b->mode = mode;
+  b->tile = tile;
+  b->occ = ctas_per_sm;
+  b->hash_factor = hash_factor;
+  return SWCS_OK;
+}
+
 int swcs_batch_build(swcs_batch* b, int autotune) {
   if (!b || b->inst.empty()) return bfail(b, SWCS_ERR_INVALID_ARG, "batch_build: no instances");
+  if (!autotune && b->mode == 0) return batch_build_persistent(b, b->tile, b->occ, b->hash_factor);
+  if (autotune && b->mode == 0) {
+    // autotuner of the persistent launch: items per tile, CTAs per SM and the
+    // alpha-string table's size (capacity = factor x state bound), timed whole
+    const int tiles[] = {2048, 4096, 8192, 16384};
+    const int occs[] = {1, 2};
+    const int factors[] = {2, 4};
+    double best_ms = 1e30;
+    int bt = 4096, bo = 2, bf = 2;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int t : tiles)
+      for (int o : occs)
+        for (int f : factors) {
+          if (batch_build_persistent(b, t, o, f)) continue;
+          cudaGraphLaunch(b->exec, b->origin);  // warm-up
+          if (batch_check(b)) continue;
+          float best = 1e30f;
+          for (int rep = 0; rep < 2; ++rep) {
+            cudaEventRecord(e0, b->origin);
+            cudaGraphLaunch(b->exec, b->origin);
+            cudaEventRecord(e1, b->origin);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best = std::min(best, ms);
+          }
+          if (best < best_ms) {
+            best_ms = best;
+            bt = t;
+            bo = o;
+            bf = f;
+          }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_ms >= 1e30) return bfail(b, SWCS_ERR_CUDA, "batch autotune: no configuration ran");
+    b->tuned_ms = (float)best_ms;
+    return batch_build_persistent(b, bt, bo, bf);
+  }
   if (!autotune) return batch_capture(b, b->share, b->cluster);
   // autotuner: device share per unit of work and cluster size of the row
   // sweep, timed on the whole graph
@@ -1904,12 +2115,34 @@ int swcs_batch_results(swcs_batch* b, int i, double* h_e, double* h_n2, double* 
   return SWCS_OK;
 }
 
-int swcs_batch_tuning(swcs_batch* b, double* h_out4) {
-  if (!b || !h_out4) return SWCS_ERR_INVALID_ARG;
-  h_out4[0] = b->share;
-  h_out4[1] = b->cluster;
-  h_out4[2] = b->tuned_ms;
-  h_out4[3] = (double)b->inst.size();
+int swcs_batch_tuning(swcs_batch* b, double* h_out8) {
+  if (!b || !h_out8) return SWCS_ERR_INVALID_ARG;
+  h_out8[0] = b->mode;
+  h_out8[1] = b->tile;
+  h_out8[2] = b->occ;
+  h_out8[3] = b->hash_factor;
+  h_out8[4] = b->tuned_ms;
+  h_out8[5] = (double)b->inst.size();
+  h_out8[6] = b->share;
+  h_out8[7] = b->cluster;
+  return SWCS_OK;
+}
+
+int swcs_batch_run_serial(swcs_batch* b) {
+  if (!b || b->inst.empty()) return bfail(b, SWCS_ERR_INVALID_ARG, "batch_run_serial: no instances");
+  for (size_t i = 0; i < b->inst.size(); ++i) {
+    swcs_ctx* c = b->inst[i];
+    const cudaStream_t own = c->st;
+    c->st = b->origin;  // every instance's kernels back to back on one stream, no synchronisation between them
+    c->opt_gate_threads = kAnsatzThreads;
+    c->opt_gate_blocks = 0;
+    c->opt_cluster = 2;
+    c->opt_row_clusters = 0;
+    int r = run_gates(c, (const uint8_t*)c->ops_dev.p, (const double*)c->cs_dev.p, b->n_ops[i], b->n_keep[i], true);
+    if (!r) r = sweep_rows(c, (double*)c->gdev.p, b->max_state[i], true);
+    c->st = own;
+    if (r) return bfail(b, r == 1 ? SWCS_ERR_INVALID_ARG : r, "batch_run_serial: " + c->err);
+  }
   return SWCS_OK;
 }
 

@@ -189,6 +189,71 @@ cudaError_t row_sweep_max_clusters(int threads, int occ, int gsz, size_t smem, i
 cudaError_t launch_row_sweep(const RowArgs& a, int threads, int occ, int gsz, int n_clusters, size_t smem,
                              cudaStream_t st);
 cudaError_t launch_group_state(const GroupArgs& g, cudaStream_t st);
+// State of the top-N radix select (gate kernel: every CTA keeps an identical copy in shared memory;
+// batched kernel: one copy per instance in global memory).
+struct SelState {
+  unsigned long long prefix;   // |c| bits decided so far
+  unsigned long long kprefix;  // bitstring bits decided so far (tie mode)
+  long long need;              // rank still to place within the current bucket
+  int shift;                   // lowest bit of the last decided |c| digit
+  int kshift;                  // lowest bit of the last decided key digit
+  int mode;                    // 0 none (keep all nonzero), 1 cut on |c|, 2 cut on |c| then key
+  int pass;                    // passes run
+  int bin;                     // result of the last bin search
+  long long cum, cnt;          // entries before that bin in selection order, entries in it
+};
+
+// ---------------------------------------------------------------------------
+// Batched persistent launch (swcs_batch.cu).  Every instance runs through a
+// chain of phases -- initial tables; per gate the gate pass, the select passes
+// still needed and the compaction; the grouping by alpha string; the beta-single
+// tables; the row sweep, one target alpha string per tile; the finish -- and
+// each phase is split into tiles.  One persistent kernel drains all instances'
+// tiles: a CTA takes the next tile of some instance's current phase from that
+// instance's (phase, next tile) word; the CTA that finishes a phase's last tile
+// runs its epilogue and publishes the next phase.
+enum BatchPhase : int {
+  kPhInit = 0, kPhBuild0, kPhGate, kPhSelect, kPhCompact, kPhGroupClear, kPhGroupInsert, kPhGroupIds,
+  kPhGroupCount, kPhGroupScan, kPhGroupScatter, kPhRbeta, kPhRow, kPhFinish, kPhDone
+};
+
+struct BatchInst {
+  AnsatzArgs ga;       // gate sequence: state, tables, ops, cos/sin, n_keep, counters, histograms, error word
+  GroupArgs gr;        // grouping by alpha string (gr.n unused: the phase passes the state size)
+  RowArgs ra;          // row sweep (ra.rows unused: every CTA has its own row)
+  int n_ops;
+  int tile;            // items per tile of the element-wise phases
+  int ks, nvs, m, packed;
+  uint64_t acap;       // alpha-string table capacity
+  double* g;           // pool gradient [pool_size]
+  int64_t pool_size;
+  double* eout;        // E, <psi|psi>
+};
+
+// One published phase of an instance (two slots, by parity of the phase number).
+struct BatchSlot {
+  unsigned phase;      // phase number this slot describes
+  int type;            // BatchPhase
+  unsigned ntiles;
+  int gate, pass;
+  long long n, m;      // state size entering the gate, merged size
+};
+
+struct BatchSched {
+  unsigned long long word;  // phase number << 32 | next tile
+  unsigned done;            // tiles of the current phase finished
+  int tab_cur;
+  unsigned ep;              // epoch of tab[tab_cur]'s build
+  int pad;
+  BatchSlot slot[2];
+  SelState sel;             // the current gate's radix select
+};
+
+size_t batch_dyn_smem(int max_ent_s, int max_ent_d, int t_same, int touched_words);
+int batch_blocks_per_sm(size_t dyn_smem);
+cudaError_t launch_batch(const BatchInst* d_inst, BatchSched* d_sched, int n_inst, double* d_rows, int64_t row_stride,
+                         int* d_status, int nblocks, size_t dyn_smem, uint64_t timeout_ns, cudaStream_t st);
+
 // Selected alpha-beta doubles per alpha pair for the screened sweep (see RowArgs::screen).
 cudaError_t launch_screen_lists(const int* kab, int m, const uint32_t* sel_bits, int* ab_cnt, uint2* ab_list,
                                 cudaStream_t st);

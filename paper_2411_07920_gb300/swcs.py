@@ -67,7 +67,9 @@ _SIGS = {
     "swcs_batch_last_error": ([_vp], ctypes.c_char_p),
     "swcs_batch_add": ([_vp, _vp, _vp, _i, _i, _vp, _vp, _i, _i64, ctypes.POINTER(_i)], _i),
     "swcs_batch_build": ([_vp, _i], _i),
+    "swcs_batch_set_tuning": ([_vp, _i, _i, _i, _i], _i),
     "swcs_batch_run": ([_vp], _i),
+    "swcs_batch_run_serial": ([_vp], _i),
     "swcs_batch_size": ([_vp, ctypes.POINTER(_i)], _i),
     "swcs_batch_pool_size": ([_vp, _i, _p64], _i),
     "swcs_batch_results": ([_vp, _i, _pd, _pd, _vp], _i),
@@ -100,7 +102,9 @@ for _name, (_args, _res) in _SIGS.items():
 
 
 class Batch:
-    """Many independent instances evaluated by one graph launch (``swcs_batch``)."""
+    """Many independent instances evaluated by one launch (``swcs_batch``): one
+    persistent kernel draining (instance, phase, tile) work items (mode 0), or a
+    graph of per-instance kernel branches (mode 1)."""
 
     def __init__(self, stream=None):
         if stream is None:
@@ -115,6 +119,7 @@ class Batch:
             raise SwcsError(r, "swcs_batch_create failed")
         self._h = h
         self.pool_sizes = []
+        self.shapes = []  # (n_so, n_elec, gates, N_keep bucket) of each instance: the tuning cache key
 
     def _ck(self, r):
         if r != 0:
@@ -131,13 +136,52 @@ class Batch:
         n = ctypes.c_int64()
         self._ck(lib.swcs_batch_pool_size(self._h, idx.value, ctypes.byref(n)))
         self.pool_sizes.append(n.value)
+        self.shapes.append((int(n_so), int(n_elec), len(theta), int(n_keep).bit_length() if n_keep > 0 else 0))
         return idx.value
 
-    def build(self, autotune=True):
+    def set_tuning(self, mode=0, tile=4096, ctas_per_sm=2, hash_factor=2):
+        self._ck(lib.swcs_batch_set_tuning(self._h, int(mode), int(tile), int(ctas_per_sm), int(hash_factor)))
+
+    def cache_key(self):
+        """The batch's shape: sorted (n_so, n_elec, gates, N_keep bucket) of its instances."""
+        import hashlib
+        return hashlib.sha256(repr(sorted(self.shapes)).encode()).hexdigest()[:20]
+
+    def build(self, autotune=True, cache_path=None):
+        """Sizes buffers and captures the launch.  autotune: time candidate
+        settings first.  cache_path: a JSON file of tuned settings keyed by
+        the batch's shape -- a hit skips the timing, a miss stores its result."""
+        import json
+        import os
+        key = self.cache_key()
+        cache = {}
+        if cache_path and os.path.exists(cache_path):
+            with open(cache_path) as f:
+                cache = json.load(f)
+        if autotune and key in cache:
+            t = cache[key]
+            self.set_tuning(t["mode"], t["tile"], t["ctas_per_sm"], t["hash_factor"])
+            self._ck(lib.swcs_batch_build(self._h, 0))
+            self.from_cache = True
+            return
+        self.from_cache = False
         self._ck(lib.swcs_batch_build(self._h, 1 if autotune else 0))
+        if autotune and cache_path:
+            t = self.tuning()
+            cache[key] = {k: t[k] for k in ("mode", "tile", "ctas_per_sm", "hash_factor", "tuned_ms")}
+            d = os.path.dirname(os.path.abspath(cache_path))
+            os.makedirs(d, exist_ok=True)
+            tmp = cache_path + f".tmp{os.getpid()}"
+            with open(tmp, "w") as f:
+                json.dump(cache, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache_path)
 
     def run(self):
         self._ck(lib.swcs_batch_run(self._h))
+
+    def run_serial(self):
+        """Every instance's own kernels back to back on the batch's stream."""
+        self._ck(lib.swcs_batch_run_serial(self._h))
 
     def results(self, i):
         e, n2 = ctypes.c_double(), ctypes.c_double()
@@ -146,9 +190,10 @@ class Batch:
         return e.value, n2.value, g
 
     def tuning(self):
-        out = np.zeros(4)
+        out = np.zeros(8)
         self._ck(lib.swcs_batch_tuning(self._h, _ptr(out)))
-        return dict(share=out[0], cluster=int(out[1]), graph_ms=out[2], instances=int(out[3]))
+        return dict(mode=int(out[0]), tile=int(out[1]), ctas_per_sm=int(out[2]), hash_factor=int(out[3]),
+                    tuned_ms=float(out[4]), instances=int(out[5]), share=float(out[6]), cluster=int(out[7]))
 
     def close(self):
         if getattr(self, "_h", None):
