@@ -379,6 +379,12 @@ const char* swcs_batch_last_error(const swcs_batch* b);
 int swcs_batch_add(swcs_batch* b, const double* h_h, const double* h_g, int n_so, int n_elec, const uint8_t* h_ops,
                    const double* h_theta, int n_ops, int64_t n_keep, int* index_out);
 int swcs_batch_set_tuning(swcs_batch* b, int mode, int tile, int ctas_per_sm, int hash_factor);
+/* Options of the next build: "wait_timeout_ms" bounds the persistent kernel's
+ * wait for work (default 2000; running out: SWCS_ERR_TIMEOUT from the next
+ * synchronising call, every CTA leaves); "test_stall_instance" (test hook, -1
+ * off) publishes that instance's first phase in a form no CTA takes, so the
+ * others finish and the bounded wait runs out without any fault. */
+int swcs_batch_set_option(swcs_batch* b, const char* name, int64_t value);
 int swcs_batch_build(swcs_batch* b, int autotune);
 int swcs_batch_run(swcs_batch* b);
 int swcs_batch_run_serial(swcs_batch* b);

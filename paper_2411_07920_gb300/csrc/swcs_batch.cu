@@ -472,7 +472,10 @@ __device__ void epilogue(const BatchInst& I, BatchSched& S, const BatchTask& k, 
 }
 
 // ---------------------------------------------------------------- the persistent kernel
-// status[0]: instances finished; status[1]: a bounded wait for work ran out.
+// status[0]: instances finished; status[1]: a bounded wait for work ran out;
+// status[2..3]: global time of the last phase published (the wait is bounded by
+// the time since then, so CTAs idle behind a long phase of another instance do
+// not give up while work is still moving).
 __global__ void __launch_bounds__(kBatchThreads, 2)
 batch_kernel(const BatchInst* __restrict__ insts, BatchSched* scheds, int n_inst, double* rows, int64_t row_stride,
              int* status, uint64_t timeout_ns) {
@@ -527,10 +530,15 @@ batch_kernel(const BatchInst* __restrict__ insts, BatchSched* scheds, int n_inst
           found = true;
         }
         if (!found) {
-          if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > timeout_ns) {
-            atomicCAS(&status[1], 0, 1);
-            task.exit = 1;
-            break;
+          if ((++spins & 63u) == 0) {
+            const uint64_t last = ld_key_relaxed((const uint64_t*)(status + 2));
+            const uint64_t ref = last > t0 ? last : t0;
+            const uint64_t now = globaltimer_ns();  // another SM's stamp may read a little ahead of this one
+            if (now > ref && now - ref > timeout_ns) {
+              atomicCAS(&status[1], 0, 1);
+              task.exit = 1;
+              break;
+            }
           }
           __nanosleep(256);
         }
@@ -624,6 +632,7 @@ batch_kernel(const BatchInst* __restrict__ insts, BatchSched* scheds, int n_inst
         S.done = 0;
         __threadfence();
         atomicExch(&S.word, (unsigned long long)next.phase << 32);
+        atomicMax((unsigned long long*)(status + 2), (unsigned long long)globaltimer_ns());
         if (next.type == kPhDone) atomicAdd(&status[0], 1);
       }
     }

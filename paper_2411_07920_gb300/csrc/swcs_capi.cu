@@ -1701,6 +1701,8 @@ struct swcs_batch {
   int* d_status = nullptr;
   size_t rows_bytes = 0, inst_bytes = 0;
   int nblocks = 0;
+  uint64_t timeout_ns = kTimeoutNs;  // bound of the persistent kernel's wait for work
+  int stall_instance = -1;           // test hook: this instance's first phase is never picked up
 };
 
 namespace {
@@ -1847,6 +1849,7 @@ int batch_build_persistent(swcs_batch* b, int tile, int occ, int hash_factor) {
     S.slot[0].ntiles = (unsigned)((c->tab_mask + 1 + tile - 1) / tile);
     S.slot[1].phase = 0xFFFFFFFFu;
     S.slot[1].type = kPhDone;
+    if (i == b->stall_instance) S.slot[0].phase = 1;  // never matches the phase word: no CTA takes its tiles
   }
   const int bps = std::min(occ, batch_blocks_per_sm(dyn));
   if (bps <= 0) return bfail(b, SWCS_ERR_NO_DEVICE, "batch: the persistent kernel cannot be resident on this device");
@@ -1866,7 +1869,7 @@ int batch_build_persistent(swcs_batch* b, int tile, int occ, int hash_factor) {
   if (cudaMemcpy(b->d_inst, hi.data(), n * sizeof(BatchInst), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b->d_sched0, hs.data(), n * sizeof(BatchSched), cudaMemcpyHostToDevice) != cudaSuccess)
     return bfail(b, SWCS_ERR_CUDA, "batch: descriptor upload failed");
-  const uint64_t timeout = b->inst[0]->opt_timeout_ns;
+  const uint64_t timeout = b->timeout_ns;
   cudaError_t e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed);
   if (e != cudaSuccess) return bfail(b, SWCS_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
   cudaMemcpyAsync(b->d_sched, b->d_sched0, n * sizeof(BatchSched), cudaMemcpyDeviceToDevice, b->origin);
@@ -1983,6 +1986,22 @@ int swcs_batch_add(swcs_batch* b, const double* h_h, const double* h_g, int n_so
   b->n_ops.push_back(n_ops);
   batch_drop_graph(b);
   if (index_out) *index_out = (int)b->inst.size() - 1;
+  return SWCS_OK;
+}
+
+int swcs_batch_set_option(swcs_batch* b, const char* name, int64_t value) {
+  if (!b || !name) return SWCS_ERR_INVALID_ARG;
+  const std::string k = name;
+  if (k == "wait_timeout_ms") {
+    if (value < 1 || value > 60000) return bfail(b, SWCS_ERR_INVALID_ARG, "wait_timeout_ms must be 1..60000");
+    b->timeout_ns = (uint64_t)value * 1000000ull;
+  } else if (k == "test_stall_instance") {
+    if (value < -1 || value >= (int64_t)b->inst.size()) return bfail(b, SWCS_ERR_INVALID_ARG, "test_stall_instance out of range");
+    b->stall_instance = (int)value;
+  } else {
+    return bfail(b, SWCS_ERR_INVALID_ARG, "unknown batch option " + k);
+  }
+  batch_drop_graph(b);
   return SWCS_OK;
 }
 

@@ -68,6 +68,7 @@ _SIGS = {
     "swcs_batch_add": ([_vp, _vp, _vp, _i, _i, _vp, _vp, _i, _i64, ctypes.POINTER(_i)], _i),
     "swcs_batch_build": ([_vp, _i], _i),
     "swcs_batch_set_tuning": ([_vp, _i, _i, _i, _i], _i),
+    "swcs_batch_set_option": ([_vp, ctypes.c_char_p, _i64], _i),
     "swcs_batch_run": ([_vp], _i),
     "swcs_batch_run_serial": ([_vp], _i),
     "swcs_batch_size": ([_vp, ctypes.POINTER(_i)], _i),
@@ -138,6 +139,9 @@ class Batch:
         self.pool_sizes.append(n.value)
         self.shapes.append((int(n_so), int(n_elec), len(theta), int(n_keep).bit_length() if n_keep > 0 else 0))
         return idx.value
+
+    def set_option(self, name, value):
+        self._ck(lib.swcs_batch_set_option(self._h, name.encode(), int(value)))
 
     def set_tuning(self, mode=0, tile=4096, ctas_per_sm=2, hash_factor=2):
         self._ck(lib.swcs_batch_set_tuning(self._h, int(mode), int(tile), int(ctas_per_sm), int(hash_factor)))

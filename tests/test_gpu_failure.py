@@ -48,3 +48,30 @@ def test_hashed_sweep_regrows_an_undersized_table(S):
     go = O.pool_gradients(w.n_so, w.h, w.g, *O.apply_ansatz(w.n_so, w.n_e, w.ops, w.theta, 800))
     assert np.abs(g - go).max() < TOL
     c.close()
+
+
+def test_batch_wait_for_work_is_bounded():
+    """One instance of a persistent batched launch is never picked up (test
+    hook): the others finish, the idle CTAs' wait for work runs out after the
+    bound, the run reports SWCS_ERR_TIMEOUT, and the batch then runs normally."""
+    from paper_2411_07920_gb300 import swcs
+    specs = [(12, 4, 10, 201, 0), (16, 6, 25, 202, 120), (20, 6, 40, 203, 400)]
+    ws = [I.small_case(*sp[:4], n_keep=sp[4]) for sp in specs]
+    b = swcs.Batch()
+    for w in ws:
+        b.add(w.h, w.g, w.n_so, w.n_e, w.ops, w.theta, w.n_keep)
+    b.set_option("wait_timeout_ms", 100)
+    b.set_option("test_stall_instance", 1)
+    b.build(autotune=False)
+    b.run()
+    with pytest.raises(swcs.SwcsError) as ei:
+        b.results(0)
+    assert ei.value.code == -4  # SWCS_ERR_TIMEOUT
+    b.set_option("test_stall_instance", -1)
+    b.build(autotune=False)
+    b.run()
+    for i, w in enumerate(ws):
+        e, n2, g = b.results(i)
+        ko, ao = O.apply_ansatz(w.n_so, w.n_e, w.ops, w.theta, w.n_keep)
+        assert abs(e - O.energy(w.n_so, w.h, w.g, ko, ao)[0]) < 1e-10
+    b.close()
