@@ -49,9 +49,9 @@ def parse(argv=None):
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--sweep", type=int, default=0, help="0 auto, 1 hashed external table, 2 alpha-string rows")
-    p.add_argument("--cluster", type=int, default=2, help="CTAs per alpha-string row cluster")
+    p.add_argument("--cluster", type=int, default=1, help="CTAs per alpha-string row cluster")
     p.add_argument("--rows-l2", type=int, default=0, help="1: cap concurrent rows to about half of L2")
-    p.add_argument("--threads", type=int, default=512, help="threads per CTA of the row sweep")
+    p.add_argument("--threads", type=int, default=1024, help="threads per CTA of the row sweep")
     p.add_argument("--row-clusters", type=int, default=0, help="clusters of the row sweep (0: as many as fit)")
     p.add_argument("--row-occupancy", type=int, default=2, help="resident 512-thread row-sweep CTAs per SM (1, 2 or 3)")
     p.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched leg")

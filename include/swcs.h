@@ -228,8 +228,8 @@ int swcs_probe_counts(swcs_ctx* ctx, int64_t* h_out4, int reset);
  *   "sweep"    0 automatic (default), 1 hashed external-sigma table,
  *              2 alpha-string rows (SWCS_ERR_INVALID_ARG when the sector's
  *              beta-string space exceeds 2^22 or clusters cannot launch)
- *   "cluster"  CTAs per alpha-string row in the row sweep, 1..16 (default 2)
- *   "threads"  threads per CTA of the row sweep: 128, 256 or 512 (default 512)
+ *   "cluster"  CTAs per alpha-string row in the row sweep, 1..16 (default 1)
+ *   "threads"  threads per CTA of the row sweep: 128, 256, 512 or 1024 (default 1024)
  *   "energy"   energy and sigma_D: 0 automatic (alpha-string rows when the
  *              sector allows, default), 1 probe kernel (connections of each D
  *              looked up in the state's index), 2 rows

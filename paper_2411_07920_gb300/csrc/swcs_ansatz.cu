@@ -59,11 +59,11 @@ ansatz_kernel(AnsatzArgs a) {
     keysA[0] = a.hf;
     ampsA[0] = 1.0;
   }
+  // the launch's index tables: 8-byte (epoch, position) slots in the first half of each table buffer
+  uint64_t* ct[2] = {(uint64_t*)a.tab[0], (uint64_t*)a.tab[1]};
   for (size_t i = gtid; i <= a.tab_mask; i += gstride) {
-    a.tab[0][i].key = kEmpty;
-    a.tab[0][i].idx = 0;  // epoch 0: no build
-    a.tab[1][i].key = kEmpty;
-    a.tab[1][i].idx = 0;
+    ct[0][i] = 0;  // epoch 0: no build
+    ct[1][i] = 0;
   }
   for (size_t i = gtid; i < 3 * kCtrN; i += gstride) a.ctr[i] = 0;
   for (size_t i = gtid; i < hist_set; i += gstride) a.hist[i] = 0;  // the first gate's set
@@ -73,7 +73,7 @@ ansatz_kernel(AnsatzArgs a) {
   if (!grid_barrier(a.bar, nblocks, a.err, a.timeout_ns)) return;
   uint32_t ep = 1;  // epoch of the build of tab[tab_cur]
   for (size_t i = gtid; i < (size_t)n; i += gstride) {
-    if (!ep_insert(a.tab[tab_cur], a.tab_mask, keysA[i], (uint32_t)i, ep)) set_error(a.err, kDevTableFull);
+    if (!ep_insert(ct[tab_cur], a.tab_mask, keysA[i], (uint32_t)i, ep)) set_error(a.err, kDevTableFull);
   }
   if (!grid_barrier(a.bar, nblocks, a.err, a.timeout_ns)) return;
 
@@ -82,8 +82,8 @@ ansatz_kernel(AnsatzArgs a) {
     unsigned long long* ctr = a.ctr + (g % 3) * kCtrN;
     const GateOp op = decode_op(a.ops + 5 * g);
     const double cs = a.cs[2 * g], sn = a.cs[2 * g + 1];
-    const IdxSlot* tcur = a.tab[tab_cur];
-    IdxSlot* tnxt = a.tab[tab_cur ^ 1];
+    const uint64_t* tcur = ct[tab_cur];
+    uint64_t* tnxt = ct[tab_cur ^ 1];
     const uint32_t ep_nxt = ep + 1;
     unsigned* H = a.hist + (size_t)(g & 1) * hist_set;  // this gate's histograms (pass 0 filled below)
 
@@ -112,7 +112,7 @@ ansatz_kernel(AnsatzArgs a) {
           else sbit = up ? double_phase(d, op.i0, op.i1, op.i2, op.i3) : double_phase(d, op.i2, op.i3, op.i0, op.i1);
           partner = d ^ op.mask_a ^ op.mask_c;
           const double t1 = __dmul_rn(c, cs);
-          const int64_t j = ep_lookup(tcur, a.tab_mask, partner, ep, &n_probe_slots);
+          const int64_t j = ep_lookup(tcur, a.tab_mask, keysA, partner, ep, &n_probe_slots);
           ++n_lookups;
           if (j >= 0) {
             const double t2 = __dmul_rn(ampsA[j], sn);
@@ -267,18 +267,21 @@ ansatz_kernel(AnsatzArgs a) {
     tab_cur ^= 1;
     ep = ep_nxt;
   }
-  // the output state's table in the plain form: stale slots empty, index word = position
+  // the output state's table in the plain key/index form, written into the other buffer
   {
-    IdxSlot* t = a.tab[tab_cur];
+    const uint64_t* t = ct[tab_cur];
+    IdxSlot* plain = a.tab[tab_cur ^ 1];
     for (size_t i = gtid; i <= a.tab_mask; i += gstride) {
-      const uint64_t w = t[i].idx;
+      const uint64_t w = t[i];
       if ((uint32_t)(w >> 32) == ep) {
-        t[i].idx = (uint32_t)w;
+        plain[i].key = keysA[(uint32_t)w];
+        plain[i].idx = (uint32_t)w;
       } else {
-        t[i].key = kEmpty;
-        t[i].idx = 0;
+        plain[i].key = kEmpty;
+        plain[i].idx = 0;
       }
     }
+    tab_cur ^= 1;
   }
   if (a.probe_ctr && (n_lookups | n_probe_slots)) {
     atomicAdd(&a.probe_ctr[0], (unsigned long long)n_lookups);

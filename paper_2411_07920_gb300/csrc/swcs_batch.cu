@@ -70,18 +70,16 @@ __device__ __forceinline__ void tile_range(long long count, long long per, unsig
 }
 
 // ---------------------------------------------------------------- gate sequence tiles
-// Initial tables: both index tables empty (epoch 0), the first gate's
+// Initial tables: both (epoch, position) index tables empty (epoch 0), the first gate's
 // histograms and the counters zero, the reference determinant as the state.
 __device__ void tile_init(const BatchInst& I, const BatchTask& k) {
   const AnsatzArgs& a = I.ga;
   const long long cap = (long long)a.tab_mask + 1;
   long long b, e;
   tile_range(cap, I.tile, k.tile, b, e);
-  for (long long i = b + threadIdx.x; i < e; i += blockDim.x) {
-    a.tab[0][i].key = kEmpty;
-    a.tab[0][i].idx = 0;
-    a.tab[1][i].key = kEmpty;
-    a.tab[1][i].idx = 0;
+  for (long long i = b + threadIdx.x; i < e; i += blockDim.x) {  // (epoch, position) slots, epoch 0: no build
+    ((uint64_t*)a.tab[0])[i] = 0;
+    ((uint64_t*)a.tab[1])[i] = 0;
   }
   const long long chunk = (long long)ceil_div((long long)kHistSet, k.ntiles);
   for (long long i = (long long)k.tile * chunk + threadIdx.x; i < min((long long)kHistSet, (long long)(k.tile + 1) * chunk);
@@ -105,7 +103,7 @@ __device__ void tile_gate(const BatchInst& I, const BatchSched& S, const BatchTa
   unsigned long long* ctr = a.ctr + (g % 3) * kCtrN;
   const GateOp op = decode_op(a.ops + 5 * g);
   const double cs = a.cs[2 * g], sn = a.cs[2 * g + 1];
-  const IdxSlot* tcur = a.tab[k.tab_cur];
+  const uint64_t* tcur = (const uint64_t*)a.tab[k.tab_cur];
   const long long n = k.n;
   long long b, e;
   tile_range(n, I.tile, k.tile, b, e);
@@ -140,7 +138,7 @@ __device__ void tile_gate(const BatchInst& I, const BatchSched& S, const BatchTa
         else sbit = up ? double_phase(d, op.i0, op.i1, op.i2, op.i3) : double_phase(d, op.i2, op.i3, op.i0, op.i1);
         partner = d ^ op.mask_a ^ op.mask_c;
         const double t1 = __dmul_rn(c, cs);
-        const int64_t j = ep_lookup(tcur, a.tab_mask, partner, k.ep, &probes);
+        const int64_t j = ep_lookup(tcur, a.tab_mask, a.keys_a, partner, k.ep, &probes);
         if (j >= 0) {
           const double t2 = __dmul_rn(a.amps_a[j], sn);
           out = __dadd_rn(t1, up ? apply_sign(t2, !sbit) : apply_sign(t2, sbit));
@@ -218,7 +216,7 @@ __device__ void tile_select(const BatchInst& I, const BatchSched& S, const Batch
 __device__ void tile_compact(const BatchInst& I, const BatchSched& S, const BatchTask& k) {
   const AnsatzArgs& a = I.ga;
   unsigned long long* ctr = a.ctr + (k.gate % 3) * kCtrN;
-  IdxSlot* tnxt = a.tab[k.tab_cur ^ 1];
+  uint64_t* tnxt = (uint64_t*)a.tab[k.tab_cur ^ 1];
   const uint32_t ep_nxt = k.ep + 1;
   const SelState s = k.sel;
   long long b, e;
@@ -556,7 +554,7 @@ batch_kernel(const BatchInst* __restrict__ insts, BatchSched* scheds, int n_inst
         tile_init(I, k);
         break;
       case kPhBuild0:
-        if (threadIdx.x == 0 && !ep_insert(I.ga.tab[k.tab_cur], I.ga.tab_mask, I.ga.hf, 0u, k.ep))
+        if (threadIdx.x == 0 && !ep_insert((uint64_t*)I.ga.tab[k.tab_cur], I.ga.tab_mask, I.ga.hf, 0u, k.ep))
           set_error(I.ga.err, kDevTableFull);
         break;
       case kPhGate:
@@ -643,7 +641,7 @@ batch_kernel(const BatchInst* __restrict__ insts, BatchSched* scheds, int n_inst
 }  // namespace
 
 size_t batch_dyn_smem(int max_ent_s, int max_ent_d, int t_same, int touched_words) {
-  return row_sweep_smem(max_ent_s, max_ent_d, t_same, touched_words);
+  return row_sweep_smem(max_ent_s, max_ent_d, 0, 0, t_same, touched_words);
 }
 
 int batch_blocks_per_sm(size_t dyn_smem) {

@@ -61,9 +61,9 @@ struct swcs_ctx {
   int NA = 0;
   int64_t NB = 0;
   int opt_sweep = 0;    // 0 auto, 1 hashed external table, 2 alpha-string rows
-  int opt_cluster = 2;  // CTAs per row cluster
+  int opt_cluster = 1;  // CTAs per row cluster
   int opt_rows_l2 = 0;  // cap concurrent rows to about half of L2
-  int opt_threads = 512;  // threads per CTA of the row sweep
+  int opt_threads = 1024;  // threads per CTA of the row sweep
   int opt_row_occ = 2;    // resident 512-thread CTAs per SM asked of the compiler (1, 2 or 3)
   double trunc_eps = 0.0;  // magnitude criterion of the truncation (0: off)
   int opt_energy = 0;     // energy: 0 automatic, 1 probe kernel, 2 alpha-string rows
@@ -421,7 +421,8 @@ int run_gates(swcs_ctx* c, const uint8_t* d_ops, const double* d_cs, int n_ops, 
     nblocks = (int)std::max<int64_t>(std::min<int64_t>(nblocks, want), std::min(nblocks, 8));
   }
   CK(launch_k(c, kKAnsatz, [&] { return launch_ansatz(a, nblocks, gthreads, c->st); }));
-  c->tab_cur = (int)(((unsigned)n_ops) & 1u);  // the kernel rebuilds tab[0] for the input, swaps per gate
+  // the kernel builds its input index in tab[0], swaps per gate and writes the output's plain table into the other
+  c->tab_cur = (int)((((unsigned)n_ops) & 1u) ^ 1u);
   c->have_state = true;
   c->n_state_host = -1;
   return SWCS_OK;
@@ -579,17 +580,30 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
   const int gsz = std::max(1, std::min(16, c->opt_cluster));
   const int ks = c->no, nvs = c->nv;
   const int ns = ks * nvs, ndb = (ks * (ks - 1) / 2) * (nvs * (nvs - 1) / 2);
-  const int max_s = (ns + gsz - 1) / gsz + 1, max_d = (ndb + gsz - 1) / gsz + 1;
+  // Shared-memory layouts, best first: every CTA of a cluster holds the target's whole entry lists (each
+  // stages its own share of the discovery, then the cluster merges them) or only its own share; with the
+  // touched-sector bitmap (one bit per 32-byte sector, 4 entries, of the row) or clearing whole rows.
   const int t_same = 1 + ns + ndb;
-  int twords = (int)((c->NB + 127) / 128);  // one bit per 32-byte sector (4 entries) of the row
-  size_t smem = row_sweep_smem(max_s, max_d, t_same, twords);
-  if (smem > 96 * 1024) {  // no room for the touched bitmap: clear whole rows
-    twords = 0;
-    smem = row_sweep_smem(max_s, max_d, t_same, 0);
-  }
-  if (smem > 96 * 1024) return 1;
-  int ncl = 0;
+  const int share_s = (ns + gsz - 1) / gsz + 1, share_d = (ndb + gsz - 1) / gsz + 1;
+  const int tw_full = (int)((c->NB + 127) / 128);
   const int nthr = c->opt_threads;
+  // dynamic shared memory per CTA: a 1024-thread CTA has an SM to itself, smaller CTAs share one by two
+  const size_t smem_cap = nthr == 1024 ? 200 * 1024 : 96 * 1024;
+  int max_s = 0, max_d = 0, st_s = 0, st_d = 0, twords = 0;
+  size_t smem = 0;
+  bool fits = false;
+  for (int layout = 0; layout < 4 && !fits; ++layout) {
+    const bool merged = gsz > 1 && (layout & 1) == 0;
+    twords = layout < 2 ? tw_full : 0;
+    max_s = merged ? ns + 1 : share_s;
+    max_d = merged ? ndb + 1 : share_d;
+    st_s = merged ? share_s : 0;
+    st_d = merged ? share_d : 0;
+    smem = row_sweep_smem(max_s, max_d, st_s, st_d, t_same, twords);
+    fits = smem <= smem_cap;
+  }
+  if (!fits) return 1;
+  int ncl = 0;
   if (row_sweep_max_clusters(nthr, c->opt_row_occ, gsz, smem, &ncl) != cudaSuccess || ncl <= 0) {
     cudaGetLastError();
     return 1;
@@ -628,6 +642,8 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
     return launch_rbeta(ga.gkey, ga.n, ga.rank_tab, ks, nvs, m, rbeta_packed, (uint32_t*)c->rbeta.p, c->st);
   }));
   RowArgs ra = row_args(c, ga, d_g, max_s, max_d, twords, rbeta_packed);
+  ra.stage_ent_s = st_s;
+  ra.stage_ent_d = st_d;
   ra.sel_bits = sel;
   ra.energy_only = energy_only ? 1 : 0;
   ra.sig_out = sig_out;
@@ -1485,7 +1501,8 @@ int swcs_set_option(swcs_ctx* c, const char* name, int64_t value) {
     if (value < 1 || value > 3) return fail(c, SWCS_ERR_INVALID_ARG, "row_occupancy must be 1, 2 or 3");
     c->opt_row_occ = (int)value;
   } else if (k == "threads") {
-    if (value != 128 && value != 256 && value != 512) return fail(c, SWCS_ERR_INVALID_ARG, "threads must be 128, 256 or 512");
+    if (value != 128 && value != 256 && value != 512 && value != 1024)
+      return fail(c, SWCS_ERR_INVALID_ARG, "threads must be 128, 256, 512 or 1024");
     c->opt_threads = (int)value;
   } else if (k == "rows_l2") {
     c->opt_rows_l2 = value != 0;
@@ -1807,10 +1824,10 @@ int batch_build_persistent(swcs_batch* b, int tile, int occ, int hash_factor) {
     const int ns = ks * nvs, ndb = (ks * (ks - 1) / 2) * (nvs * (nvs - 1) / 2);
     const int max_s = ns + 1, max_d = ndb + 1, t_same = 1 + ns + ndb;  // one CTA per target: all its entries
     int twords = (int)((c->NB + 127) / 128);
-    size_t smem = row_sweep_smem(max_s, max_d, t_same, twords);
+    size_t smem = row_sweep_smem(max_s, max_d, 0, 0, t_same, twords);
     if (smem > 96 * 1024) {
       twords = 0;
-      smem = row_sweep_smem(max_s, max_d, t_same, 0);
+      smem = row_sweep_smem(max_s, max_d, 0, 0, t_same, 0);
     }
     if (smem > 96 * 1024) return bfail(b, SWCS_ERR_INVALID_ARG, "batch: an instance's sector does not fit the row sweep");
     dyn = std::max(dyn, smem);
@@ -2155,7 +2172,8 @@ int swcs_batch_run_serial(swcs_batch* b) {
     c->st = b->origin;  // every instance's kernels back to back on one stream, no synchronisation between them
     c->opt_gate_threads = kAnsatzThreads;
     c->opt_gate_blocks = 0;
-    c->opt_cluster = 2;
+    c->opt_cluster = 1;  // the single-context default shape
+    c->opt_threads = 1024;
     c->opt_row_clusters = 0;
     int r = run_gates(c, (const uint8_t*)c->ops_dev.p, (const double*)c->cs_dev.p, b->n_ops[i], b->n_keep[i], true);
     if (!r) r = sweep_rows(c, (double*)c->gdev.p, b->max_state[i], true);

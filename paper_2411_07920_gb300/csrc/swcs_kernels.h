@@ -124,7 +124,8 @@ struct RowArgs {
   double* g;
   double* acc;                 // acc[0] += sum c_D sigma_D
   int* err;
-  int max_ent_s, max_ent_d;
+  int max_ent_s, max_ent_d;  // capacity of the target's entry lists (all CTAs of its cluster together)
+  int stage_ent_s, stage_ent_d;  // capacity of one CTA's share before the cluster merges them (0: one CTA per target)
   int touched_words;  // words of the per-CTA touched-sector bitmap, one bit per 4 entries (0: clear whole rows)
   const uint32_t* sel_bits;  // pool operators to evaluate (nullptr: all)
   // beta single excitations of each grouped determinant, t = occ_slot*nv + vir_slot:
@@ -184,7 +185,7 @@ struct GroupArgs {
   double* acc;  // acc[1] += sum c^2
 };
 
-size_t row_sweep_smem(int max_ent_s, int max_ent_d, int t_same, int touched_words);
+size_t row_sweep_smem(int max_ent_s, int max_ent_d, int stage_ent_s, int stage_ent_d, int t_same, int touched_words);
 cudaError_t row_sweep_max_clusters(int threads, int occ, int gsz, size_t smem, int* n_clusters);
 cudaError_t launch_row_sweep(const RowArgs& a, int threads, int occ, int gsz, int n_clusters, size_t smem,
                              cudaStream_t st);

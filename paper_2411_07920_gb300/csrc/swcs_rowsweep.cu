@@ -134,8 +134,9 @@ cudaError_t launch_rbeta(const uint64_t* gkey, const long long* n, const uint32_
   return cudaGetLastError();
 }
 
-size_t row_sweep_smem(int max_ent_s, int max_ent_d, int t_same, int touched_words) {
-  return sizeof(RowEnt) * (size_t)(max_ent_s + max_ent_d) + 4 * (size_t)t_same + 4 * (size_t)touched_words;
+size_t row_sweep_smem(int max_ent_s, int max_ent_d, int stage_ent_s, int stage_ent_d, int t_same, int touched_words) {
+  return sizeof(RowEnt) * (size_t)(max_ent_s + max_ent_d + stage_ent_s + stage_ent_d) + 4 * (size_t)t_same +
+         4 * (size_t)touched_words;
 }
 
 namespace {
@@ -179,14 +180,16 @@ cudaError_t launch_t(const RowArgs& a, int gsz, int n_clusters, size_t smem, cud
 }
 }  // namespace
 
-// threads: 128, 256 or 512 per CTA; resident 512-thread CTAs per SM requested
-// from the compiler: 1 (no register cap), 2 (64 registers) or 3 (40 registers)
+// threads: 128, 256, 512 or 1024 per CTA; resident 512-thread CTAs per SM requested
+// from the compiler: 1 (no register cap), 2 (64 registers) or 3 (40 registers); 1024-thread CTAs: one
+// per SM (64 registers)
 cudaError_t row_sweep_max_clusters(int threads, int occ, int gsz, size_t smem, int* n_clusters) {
   if (threads == 128) return max_clusters_t<128, 1>(gsz, smem, n_clusters);
   if (threads == 256) return max_clusters_t<256, 1>(gsz, smem, n_clusters);
   if (threads == 512) return occ >= 3 ? max_clusters_t<512, 3>(gsz, smem, n_clusters)
                              : occ == 2 ? max_clusters_t<512, 2>(gsz, smem, n_clusters)
                                         : max_clusters_t<512, 1>(gsz, smem, n_clusters);
+  if (threads == 1024) return max_clusters_t<1024, 1>(gsz, smem, n_clusters);
   return cudaErrorInvalidValue;
 }
 
@@ -197,6 +200,7 @@ cudaError_t launch_row_sweep(const RowArgs& a, int threads, int occ, int gsz, in
   if (threads == 512) return occ >= 3 ? launch_t<512, 3>(a, gsz, n_clusters, smem, st)
                              : occ == 2 ? launch_t<512, 2>(a, gsz, n_clusters, smem, st)
                                         : launch_t<512, 1>(a, gsz, n_clusters, smem, st);
+  if (threads == 1024) return launch_t<1024, 1>(a, gsz, n_clusters, smem, st);
   return cudaErrorInvalidValue;
 }
 

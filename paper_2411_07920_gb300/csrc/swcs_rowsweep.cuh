@@ -17,7 +17,7 @@ namespace swcs {
 
 namespace {
 
-constexpr int kRowMaxWarps = 16;  // CTA sizes 128, 256 or 512 threads
+constexpr int kRowMaxWarps = 32;  // CTA sizes 128, 256, 512 or 1024 threads
 constexpr int kSameChunk = 128;  // targets of one determinant per work item (4 per lane)
 constexpr int kDblChunk = 1;     // determinants per alpha-double work item
 
@@ -57,18 +57,22 @@ struct RowShared {
   uint8_t occx[kMaxSpin], virx[kMaxSpin];
   uint8_t bocc[kRowMaxWarps][kMaxSpin], bvir[kRowMaxWarps][kMaxSpin];  // beta spatial lists per warp
   uint8_t occ_all[kRowMaxWarps][64];
-  int n_s, n_d;              // entries found
+  int n_s, n_d;              // entries of the target (all CTAs of the cluster)
+  int n_s_loc, n_d_loc;      // entries this CTA found (its staged share)
   uint32_t tot_s, tot_d;     // work items (singles: entry x determinant; doubles: entry x chunk)
   long long gx_off, gx_cnt;  // the alpha group of X itself
   unsigned scan_tmp[kRowMaxWarps];
   double red[kRowMaxWarps];
 };
 
-// Dynamic shared memory: entry lists, the decode table of X's own targets and
-// the bitmap of row entries this CTA touched.
+// Dynamic shared memory: entry lists, the staged share of the discovery, the
+// decode table of X's own targets and the bitmap of row entries this CTA
+// touched.
 struct RowDyn {
-  RowEnt* ents_s;
+  RowEnt* ents_s;  // the target's entries, in the same order in every CTA of the cluster
   RowEnt* ents_d;
+  RowEnt* stage_s;  // entries this CTA found (the lists themselves when one CTA sweeps a target)
+  RowEnt* stage_d;
   uint32_t* same_tab;  // target t >= 1 of a determinant in X's group: o1 | o2<<8 | v1<<16 | v2<<24 (o2 = 255: single)
   unsigned* touched;   // NB bits (nullptr: clear whole rows)
 };
@@ -298,7 +302,7 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
         const int i1 = sh.bocc[warp][code & 255], i2 = sh.bocc[warp][(code >> 8) & 255];
         const int j1 = sh.bvir[warp][(code >> 16) & 255], j2 = sh.bvir[warp][code >> 24];
         re[u] = str_rank(A.rank_tab, ks, db ^ (1u << i1) ^ (1u << i2) ^ (1u << j1) ^ (1u << j2));
-        if (SCATTER && !take(touched, filt, re[u])) { ok[u] = false; continue; }
+        if (SCATTER && filt && !take(touched, true, re[u])) { ok[u] = false; continue; }
         const int p = 2 * i1 + 1, q = 2 * i2 + 1, r = 2 * j1 + 1, s2 = 2 * j2 + 1;
         const int pa = pair_index(p, q, A.H.n), pb = pair_index(r, s2, A.H.n);
         sg[u] = double_phase(d, p, q, r, s2);
@@ -308,10 +312,20 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
           const bool down = pa > pb;
           ix[u] = __ldg(&A.H.opd[down ? (size_t)pb * A.H.npairs + pa : (size_t)pa * A.H.npairs + pb]);
           sg[u] ^= (int)down;
-          if (!selected(A, ix[u])) { ok[u] = false; continue; }
-          if (MARK) { mark_sector(dy.touched, re[u]); ok[u] = false; continue; }
-          val[u] = row[re[u]];
+          if (!MARK) val[u] = row[re[u]];  // read alongside the operator index, used only if selected
         }
+      }
+      if (!SCATTER) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (!ok[u]) continue;
+          if (!selected(A, ix[u])) ok[u] = false;
+          else if (MARK) { mark_sector(dy.touched, re[u]); ok[u] = false; }
+        }
+      } else if (!filt) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (ok[u]) take(touched, false, re[u]);
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -324,7 +338,12 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
   }
   // ---------------- alpha-single neighbours, the alpha single itself: one determinant per lane.  Each
   // lane sums its own Fock element h_qp + sum_{k in D} <qk||pk> (no warp reduction per determinant)
-  for (uint32_t t0 = (uint32_t)warp * 32; t0 < sh.tot_s; t0 += kRowThreads) {
+  // items of the neighbour groups: split over the cluster when every CTA holds the target's whole lists,
+  // else each CTA works through the groups it found
+  const bool merged = A.stage_ent_s > 0;
+  const uint32_t gwarp = (uint32_t)((merged ? crank * kRowWarps : 0) + warp);
+  const uint32_t gwarps = (uint32_t)((merged ? gsz : 1) * kRowWarps);
+  for (uint32_t t0 = gwarp * 32; t0 < sh.tot_s; t0 += gwarps * 32) {
     int e1 = warp_find_entry(dy.ents_s, sh.n_s, t0, lane);
     const int ej = e1 + lane;
     const uint32_t st = (lane > 0 && ej < sh.n_s) ? dy.ents_s[ej].flat - t0 : 32u;
@@ -376,8 +395,8 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
       wb_n[u] = t2 < nsb ? __ldg(&rb[t2]) : 0u;
     }
   };
-  if ((uint32_t)warp < sh.tot_s) fetch((uint32_t)warp);
-  for (uint32_t t = warp; t < sh.tot_s; t += kRowWarps) {
+  if (gwarp < sh.tot_s) fetch(gwarp);
+  for (uint32_t t = gwarp; t < sh.tot_s; t += gwarps) {
     const RowEnt en = dy.ents_s[e];
     const long long di = di_n;
     const uint64_t d = d_n;
@@ -385,7 +404,7 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
     uint32_t wb0[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) wb0[u] = wb_n[u];
-    if (t + kRowWarps < sh.tot_s) fetch(t + kRowWarps);
+    if (t + gwarps < sh.tot_s) fetch(t + gwarps);
     if (!packed) warp_lists(sh, warp, lane, d, m);  // unpacked entries: pair indices from the beta lists
     const int pa = en.o[0], pb = en.o[2];  // alpha spin-orbitals: removed, added
     // alpha-beta doubles: phase = (beta single on D) ^ (alpha single on D) ^ (index-only bit in the tables);
@@ -460,16 +479,21 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
           re[u] = 0;
           kk[u] = 0;
           sb[u] = 0;
-          if (ok[u]) {
+          sv[u] = 0.0;
+          if (ok[u]) {  // the operator index and the row entry read together
             re[u] = wv[u] & rmask;
             sb[u] = (int)(wv[u] >> 31) ^ sa;
             kk[u] = __ldg(&A.kab[base + pair_ij(u)]);
-            const int k = kk[u] & 0x7FFFFFFF;
-            if (A.sel_bits && !((__ldg(&A.sel_bits[k >> 5]) >> (k & 31)) & 1u)) ok[u] = false;
+            sv[u] = row[re[u]];
           }
         }
+        if (A.sel_bits) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) sv[u] = ok[u] ? row[re[u]] : 0.0;
+          for (int u = 0; u < 4; ++u) {
+            const int k = kk[u] & 0x7FFFFFFF;
+            if (ok[u] && !((__ldg(&A.sel_bits[k >> 5]) >> (k & 31)) & 1u)) ok[u] = false;
+          }
+        }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
           if (ok[u]) atomicAdd(&A.g[kk[u] & 0x7FFFFFFF], apply_sign(cd * sv[u], sb[u] ^ (int)((unsigned)kk[u] >> 31)));
@@ -483,7 +507,7 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
   // so the starts are distinct and the walk below takes no step).  Every item of an entry is the same
   // pool operator, so the gather sums each entry's lanes in the warp and its first lane adds the total.
   const int npairs = A.H.npairs, n = A.H.n;
-  for (uint32_t t0 = (uint32_t)warp * 32; t0 < sh.tot_d; t0 += kRowThreads) {
+  for (uint32_t t0 = gwarp * 32; t0 < sh.tot_d; t0 += gwarps * 32) {
     int e = warp_find_entry(dy.ents_d, sh.n_d, t0, lane);
     const int ej = e + lane;
     const uint32_t st = (lane > 0 && ej < sh.n_d) ? dy.ents_d[ej].flat - t0 : 32u;
@@ -500,22 +524,32 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
       const int pa = pair_index(p, q, n), pb = pair_index(r, s2, n);
       const uint32_t rd = __ldg(&A.grank[di]);
       if (SCATTER) {
-        if (take(touched, filt, rd)) {
+        if (filt) {  // energy only: most pairs are skipped, so test before the other loads
+          if (take(touched, true, rd)) {
+            const double gv = __ldg(&A.H.G[(size_t)pa * npairs + pb]);
+            const uint64_t d = __ldg(&A.gkey[di]);
+            const double cd = __ldg(&A.gamp[di]);
+            atomicAdd(&row[rd], apply_sign(gv, double_phase(d, p, q, r, s2)) * cd);
+          }
+        } else {  // every load issued together, off the rank's dependency chain
           const double gv = __ldg(&A.H.G[(size_t)pa * npairs + pb]);
           const uint64_t d = __ldg(&A.gkey[di]);
           const double cd = __ldg(&A.gamp[di]);
+          take(touched, false, rd);
           atomicAdd(&row[rd], apply_sign(gv, double_phase(d, p, q, r, s2)) * cd);
         }
       } else {
         const bool down = pa > pb;
         k = __ldg(&A.H.opd[down ? (size_t)pb * npairs + pa : (size_t)pa * npairs + pb]);
-        if (!selected(A, k)) k = -1;
         if (MARK) {
+          if (!selected(A, k)) k = -1;
           if (k >= 0) mark_sector(dy.touched, rd);
-        } else if (k >= 0) {
+        } else {  // the determinant and its row entry read alongside the operator index
           const uint64_t d = __ldg(&A.gkey[di]);
           const double cd = __ldg(&A.gamp[di]);
-          v = apply_sign(cd * row[rd], double_phase(d, p, q, r, s2) ^ (int)down);
+          const double sv = row[rd];
+          if (!selected(A, k)) k = -1;
+          if (k >= 0) v = apply_sign(cd * sv, double_phase(d, p, q, r, s2) ^ (int)down);
         }
       }
     }
@@ -537,12 +571,17 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
 // (the pool sweep's launch) or a single CTA (the batched persistent kernel).
 struct ClusterSync {
   cg::cluster_group cl;
-  __device__ void sync() { cl.sync(); }
-  __device__ unsigned* remote(unsigned* p, int r) { return cl.map_shared_rank(p, r); }
+  __device__ void sync() {
+    if (cl.num_blocks() == 1) __syncthreads();  // a cluster of one CTA: the CTA barrier orders the same accesses
+    else cl.sync();
+  }
+  template <class T>
+  __device__ T* remote(T* p, int r) { return cl.map_shared_rank(p, r); }
 };
 struct BlockSync {
   __device__ void sync() { __syncthreads(); }
-  __device__ unsigned* remote(unsigned* p, int) { return p; }
+  template <class T>
+  __device__ T* remote(T* p, int) { return p; }
 };
 
 // Dynamic shared memory of a row-sweep CTA, laid out for A's sector.
@@ -552,7 +591,9 @@ __device__ __forceinline__ RowDyn row_dyn(unsigned char* dyn, const RowArgs& A) 
   RowDyn dy;
   dy.ents_s = (RowEnt*)dyn;
   dy.ents_d = dy.ents_s + A.max_ent_s;
-  dy.same_tab = (uint32_t*)(dy.ents_d + A.max_ent_d);
+  dy.stage_s = A.stage_ent_s > 0 ? dy.ents_d + A.max_ent_d : dy.ents_s;
+  dy.stage_d = A.stage_ent_s > 0 ? dy.stage_s + A.stage_ent_s : dy.ents_d;
+  dy.same_tab = (uint32_t*)(A.stage_ent_s > 0 ? dy.stage_d + A.stage_ent_d : dy.ents_d + A.max_ent_d);
   dy.touched = A.touched_words > 0 ? (unsigned*)(dy.same_tab + t_same) : nullptr;
   return dy;
 }
@@ -602,6 +643,7 @@ __device__ void row_target(const RowArgs& A, RowShared& sh, const RowDyn& dy, do
   const int n_to = ks * (ks - 1) / 2, n_tv = nvs * (nvs - 1) / 2;
   const int ns = ks * nvs, nd = n_to * n_tv;
   const int nwords = A.touched_words;
+  const bool merged = A.stage_ent_s > 0;  // the cluster merges its CTAs' entries (clusters of 2 or more)
   (void)n_to;
   const uint32_t X = probe ? __ldg(&A.probe_x[xi])
                            : A.energy_only ? even_bits(__ldg(&A.gkey[A.goff[xi]])) : A.alpha_list[xi];
@@ -614,8 +656,8 @@ __device__ void row_target(const RowArgs& A, RowShared& sh, const RowDyn& dy, do
     if (o) sh.occx[__popc(bo & below)] = (uint8_t)lane;
     else if (inr) sh.virx[__popc(bv & below)] = (uint8_t)lane;
     if (lane == 0) {
-      sh.n_s = 0;
-      sh.n_d = 0;
+      sh.n_s_loc = 0;
+      sh.n_d_loc = 0;
       const int64_t g = A.energy_only ? (int64_t)xi : idx_lookup(A.atab, A.amask, (uint64_t)X);
       sh.gx_off = g >= 0 ? A.goff[g] : 0;
       sh.gx_cnt = g >= 0 ? A.goff[g + 1] - A.goff[g] : 0;
@@ -665,20 +707,48 @@ __device__ void row_target(const RowArgs& A, RowShared& sh, const RowDyn& dy, do
       en.off = (uint32_t)A.goff[g];
       en.flat = (uint32_t)(A.goff[g + 1] - A.goff[g]);
       en.o[0] = o4[0]; en.o[1] = o4[1]; en.o[2] = o4[2]; en.o[3] = o4[3];
+      const int cap_s = merged ? A.stage_ent_s : A.max_ent_s, cap_d = merged ? A.stage_ent_d : A.max_ent_d;
       if (single) {
-        const int slot = atomicAdd(&sh.n_s, 1);
-        if (slot < A.max_ent_s) dy.ents_s[slot] = en;
+        const int slot = atomicAdd(&sh.n_s_loc, 1);
+        if (slot < cap_s) dy.stage_s[slot] = en;
       } else {
-        const int slot = atomicAdd(&sh.n_d, 1);
-        if (slot < A.max_ent_d) dy.ents_d[slot] = en;
+        const int slot = atomicAdd(&sh.n_d_loc, 1);
+        if (slot < cap_d) dy.stage_d[slot] = en;
       }
     }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    if (sh.n_s > A.max_ent_s || sh.n_d > A.max_ent_d) set_error(A.err, kDevBadState);
-    sh.n_s = min(sh.n_s, A.max_ent_s);
-    sh.n_d = min(sh.n_d, A.max_ent_d);
+    const int cap_s = merged ? A.stage_ent_s : A.max_ent_s, cap_d = merged ? A.stage_ent_d : A.max_ent_d;
+    if (sh.n_s_loc > cap_s || sh.n_d_loc > cap_d) set_error(A.err, kDevBadState);
+    sh.n_s_loc = min(sh.n_s_loc, cap_s);
+    sh.n_d_loc = min(sh.n_d_loc, cap_d);
+    if (!merged) {
+      sh.n_s = sh.n_s_loc;
+      sh.n_d = sh.n_d_loc;
+    }
+  }
+  // every CTA's share of the discovery is complete, and so is every CTA's clear of the previous target's
+  // sectors (the clear flows straight into this target's discovery)
+  sy.sync();
+  if (merged) {
+    // the cluster's entries in rank order, copied into every CTA, so that the work items of the whole
+    // target can be split evenly over all CTAs whatever the sizes of the groups each CTA found
+    int bs = 0, bd = 0;
+    for (int r = 0; r < gsz; ++r) {
+      const int ns_r = *sy.remote(&sh.n_s_loc, r), nd_r = *sy.remote(&sh.n_d_loc, r);
+      const RowEnt* ss = sy.remote(dy.stage_s, r);
+      const RowEnt* sd = sy.remote(dy.stage_d, r);
+      for (int t = threadIdx.x; t < ns_r && bs + t < A.max_ent_s; t += kRowThreads) dy.ents_s[bs + t] = ss[t];
+      for (int t = threadIdx.x; t < nd_r && bd + t < A.max_ent_d; t += kRowThreads) dy.ents_d[bd + t] = sd[t];
+      bs += ns_r;
+      bd += nd_r;
+    }
+    if (threadIdx.x == 0) {
+      if (bs > A.max_ent_s || bd > A.max_ent_d) set_error(A.err, kDevBadState);
+      sh.n_s = min(bs, A.max_ent_s);
+      sh.n_d = min(bd, A.max_ent_d);
+    }
   }
   __syncthreads();
   scan_items<kRowThreads>(sh, dy.ents_s, sh.n_s, 1, &sh.tot_s);
@@ -689,8 +759,7 @@ __device__ void row_target(const RowArgs& A, RowShared& sh, const RowDyn& dy, do
     // marked by every CTA for its share of the pairs, then merged over the cluster
     for (long long t = threadIdx.x; t < sh.gx_cnt; t += kRowThreads) mark_sector(dy.touched, __ldg(&A.grank[sh.gx_off + t]));
     row_phase<kRowThreads, kPassMark>(A, sh, dy, row, crank, gsz, e_acc);
-    // every CTA's marks are complete and the previous target's sectors cleared
-    sy.sync();
+    sy.sync();  // every CTA's marks are complete
     for (int w = threadIdx.x; w < nwords; w += kRowThreads) {
       unsigned bits = 0u;
       for (int r = 0; r < gsz; ++r)
@@ -698,10 +767,6 @@ __device__ void row_target(const RowArgs& A, RowShared& sh, const RowDyn& dy, do
       if (bits) atomicOr(&dy.touched[w], bits);
     }
     __syncthreads();
-  } else {
-    // the other CTA may still be clearing the previous target's sectors: wait for it before scattering
-    // (the clear itself flows straight into this target's discovery)
-    sy.sync();
   }
   row_phase<kRowThreads, kPassScatter>(A, sh, dy, row, crank, gsz, e_acc);
   sy.sync();

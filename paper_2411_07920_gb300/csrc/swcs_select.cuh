@@ -76,38 +76,38 @@ __device__ void find_bin(const unsigned* h, int nb, long long need, bool desc, S
   __syncthreads();
 }
 
-// Index tables of the states inside one launch carry the build's epoch in the
-// high 32 bits of their index word (positions are below 2^32), so a table is
-// never cleared between gates: a slot whose epoch is not the build's reads as
-// empty.  After the last gate the output table is rewritten in the plain form
-// (empty key ~0, index word = position) that every other kernel reads.
-__device__ __forceinline__ bool ep_insert(IdxSlot* t, uint64_t mask, uint64_t key, uint32_t pos, uint32_t ep) {
+// Index tables of the states inside one launch: 8-byte slots holding the
+// build's epoch in the high 32 bits and the determinant's position in the
+// state arrays in the low 32; the key itself is read from the state's key
+// array.  A slot whose epoch is not the build's reads as empty, so a table is
+// never cleared between gates, and two tables take half the memory of
+// key/index slots.  After the last gate the output table is written once in
+// the plain key/index form that every other kernel reads.
+__device__ __forceinline__ bool ep_insert(uint64_t* t, uint64_t mask, uint64_t key, uint32_t pos, uint32_t ep) {
   uint64_t s = mix64(key) & mask;
   const unsigned long long claim = ((unsigned long long)ep << 32) | pos;
   for (uint64_t n = 0; n <= mask; ++n) {
-    unsigned long long* w = (unsigned long long*)&t[s].idx;
+    unsigned long long* w = (unsigned long long*)&t[s];
     const unsigned long long old = ld_key_relaxed((const uint64_t*)w);
-    if ((uint32_t)(old >> 32) != ep && atomicCAS(w, old, claim) == old) {
-      t[s].key = key;
-      return true;
-    }
+    if ((uint32_t)(old >> 32) != ep && atomicCAS(w, old, claim) == old) return true;
     s = (s + 1) & mask;
   }
   return false;
 }
 
-__device__ __forceinline__ int64_t ep_lookup(const IdxSlot* __restrict__ t, uint64_t mask, uint64_t key, uint32_t ep,
-                                             unsigned* probes) {
+// Position of key in the build `ep` of table t over the state keys (-1: absent); adds the slots visited to *probes.
+__device__ __forceinline__ int64_t ep_lookup(const uint64_t* __restrict__ t, uint64_t mask, const uint64_t* keys,
+                                             uint64_t key, uint32_t ep, unsigned* probes) {
   uint64_t s = mix64(key) & mask;
   for (uint64_t n = 0; n <= mask; ++n) {
-    const IdxSlot sl = t[s];
-    if ((uint32_t)(sl.idx >> 32) != ep) {  // a slot this build never claimed ends the probe
+    const uint64_t w = t[s];
+    if ((uint32_t)(w >> 32) != ep) {  // a slot this build never claimed ends the probe
       *probes += (unsigned)n + 1u;
       return -1;
     }
-    if (sl.key == key) {
+    if (keys[(uint32_t)w] == key) {
       *probes += (unsigned)n + 1u;
-      return (int64_t)(uint32_t)sl.idx;
+      return (int64_t)(uint32_t)w;
     }
     s = (s + 1) & mask;
   }

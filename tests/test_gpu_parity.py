@@ -94,7 +94,8 @@ def test_energy_and_pool_gradient_truncated(S, n_so, n_e, n_ops, seed, n_keep):
 
 
 @pytest.mark.parametrize("sweep,cluster,threads,occ", [(1, 4, 512, 3), (2, 1, 128, 3), (2, 2, 256, 3), (2, 4, 512, 3),
-                                                       (2, 8, 512, 2), (2, 1, 512, 2), (2, 2, 512, 3), (2, 2, 512, 1)])
+                                                       (2, 8, 512, 2), (2, 1, 512, 2), (2, 2, 512, 3), (2, 2, 512, 1),
+                                                       (2, 1, 1024, 1), (2, 2, 1024, 1), (2, 4, 1024, 1)])
 @pytest.mark.parametrize("n_so,n_e,n_ops,seed,n_keep", [(16, 6, 40, 102, 150), (24, 8, 40, 107, 400),
                                                         (28, 8, 60, 104, 3000), (12, 4, 10, 1, 0)])
 def test_sweep_paths_match_oracle(S, sweep, cluster, threads, occ, n_so, n_e, n_ops, seed, n_keep):
