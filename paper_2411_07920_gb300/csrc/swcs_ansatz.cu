@@ -37,6 +37,7 @@ ansatz_kernel(AnsatzArgs a) {
   __shared__ unsigned s_hist[kBins];
   __shared__ long long s_scan[32];
   __shared__ long long s_n;
+  __shared__ unsigned long long s_base;
 
   const unsigned nblocks = gridDim.x;
   const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -234,18 +235,49 @@ ansatz_kernel(AnsatzArgs a) {
     const SelState s = sel;
 
     // ------------------------------------------------------------ P3 compaction + re-index
-    const size_t m_iter = ((size_t)m + gstride - 1) / gstride * gstride;
-    for (size_t i = gtid; i < m_iter; i += gstride) {
-      bool keep = false;
-      uint64_t k = 0;
-      double c = 0.0;
-      if (i < (size_t)m) {
-        k = keysB[i];
-        c = ampsB[i];
-        keep = keep_entry(s, k, c, a.min_abs_bits);
+    // Output positions by block, in rounds of up to 32 items per thread: each thread marks which of its
+    // items are kept, the block scans the counts and takes its range of the output with one atomic (a
+    // counter per warp would put tens of thousands of atomics per gate on one address), then the kept
+    // items are read again and written, indexed and snapshotted.
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (size_t r0 = 0; r0 < (size_t)m; r0 += (size_t)32 * gstride) {
+      uint32_t kmask = 0;
+      unsigned cnt = 0;
+      for (int it = 0; it < 32; ++it) {
+        const size_t i = r0 + (size_t)it * gstride + gtid;
+        if (i >= (size_t)m) break;
+        const uint64_t k = s.mode == 2 ? keysB[i] : 0;  // the bitstring decides only exact ties at the cut
+        if (keep_entry(s, k, ampsB[i], a.min_abs_bits)) {
+          kmask |= 1u << it;
+          ++cnt;
+        }
       }
-      const unsigned long long pos = warp_alloc(&ctr[kCtrKept], keep);
-      if (keep) {
+      unsigned inc = cnt;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const unsigned v = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += v;
+      }
+      if (lane == 31) s_scan[wid] = inc;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        long long run = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+          const long long v = s_scan[w];
+          s_scan[w] = run;
+          run += v;
+        }
+        s_base = run ? atomicAdd(&ctr[kCtrKept], (unsigned long long)run) : 0ull;
+      }
+      __syncthreads();
+      unsigned long long pos = s_base + (unsigned long long)s_scan[wid] + (inc - cnt);
+      __syncthreads();  // s_scan and s_base are rewritten next round
+      while (kmask) {
+        const int it = __ffs(kmask) - 1;
+        kmask &= kmask - 1u;
+        const size_t i = r0 + (size_t)it * gstride + gtid;
+        const uint64_t k = keysB[i];
+        const double c = ampsB[i];
         keysA[pos] = k;
         ampsA[pos] = c;
         if (!ep_insert(tnxt, a.tab_mask, k, (uint32_t)pos, ep_nxt)) set_error(a.err, kDevTableFull);
@@ -253,6 +285,7 @@ ansatz_kernel(AnsatzArgs a) {
           a.snap_keys[(size_t)g * a.snap_stride + pos] = k;
           a.snap_amps[(size_t)g * a.snap_stride + pos] = c;
         }
+        ++pos;
       }
     }
     if (!grid_barrier(a.bar, nblocks, a.err, a.timeout_ns)) return;
