@@ -391,6 +391,25 @@ def run_swcs(args):
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     gate_ms = prof.get("ansatz", (0.0, 0))[0]
     gate_dets_per_s = stats["gate_dets"] / (gate_ms / 1e3) if gate_ms > 0 else None
+    # the other two kernels of the path, on the same measured peak
+    rooflines = {}
+    gate_n = prof.get("ansatz", (0.0, 0))[1]
+    if gate_ms > 0 and gate_n > 0:
+        # per gate: read S (16 B/det), write and re-read Phi (32 B), select reads (8 B/pass), write S' (16 B),
+        # with |Phi| and |S'| taken as |S|
+        passes = stats["select_passes"] / max(stats["gates"], 1)
+        gb = (16 + 32 + 8 * passes + 16) * stats["gate_dets"] / gate_n
+        ach = gb / (gate_ms / gate_n / 1e3) / 1e9
+        rooflines["gate"] = {"kernel": "ansatz", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": ach / hbm_peak, "bytes_per_launch": gb, "select_passes_per_gate": passes,
+                             "traffic": measured_traffic("ansatz", args)}
+    if energy_ms:
+        # energy <psi|H|psi>: 16 B (key and amplitude) per connection of every determinant probed in the
+        # state, the bytes of the probe formulation (the row kernel in energy-only mode reads fewer)
+        eb = 16.0 * n_det * (n_conn + 1)
+        ach = eb / (min(energy_ms) / 1e3) / 1e9
+        rooflines["energy"] = {"kernel": "row_sweep (energy only)", "bound": "hbm", "achieved": ach, "peak": hbm_peak,
+                               "unit": "GB/s", "frac": ach / hbm_peak, "bytes_per_launch": eb, "traffic": None}
     launches = int(stats["kernel_launches"])
 
     # ------------------------------------------------------------ end to end through the host API
@@ -456,7 +475,8 @@ def run_swcs(args):
                 "config": {"workload": "52 spin-orbitals, 12 electrons, 200-gate ansatz (seed 3), "
                                        f"N={args.n_keep}, GSD pool {pool}",
                            "parallelism": f"replicas x{world}", "l2": "flushed between steps (512 MB write)"},
-                "gate_dets_per_s": gate_dets_per_s, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gate_dets_per_s": gate_dets_per_s, "roofline": roof, "rooflines": rooflines, "cpu_baseline": cpu,
+                "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "energy_ms": round(min(energy_ms), 3), "hash_probes": probes,
                 "adjoint": adjoint, "batch": batch, "screen": screen_res, "adapt": adapt_res,
                 "kernels_ms": {k: round(v[0], 3) for k, v in prof.items()},
@@ -480,25 +500,39 @@ def aggregate(total_ms, steps, world, device):
 
 
 # the launch the committed row-sweep traffic was captured on: the default workload and launch shape
-TRAFFIC_CAPTURED = dict(n_keep=1_000_000, cluster=2, rows_l2=0, threads=512, row_clusters=0, row_occupancy=2)
+TRAFFIC_CAPTURED = dict(n_keep=1_000_000, cluster=1, rows_l2=0, threads=1024, row_clusters=0)
+# kernel -> (committed ncu summary, the sources of the captured kernel)
+TRAFFIC_FILES = {
+    "row_sweep": ("profiles/row_sweep_so52_e12_N1e6.md",
+                  ["paper_2411_07920_gb300/csrc/swcs_rowsweep.cu", "paper_2411_07920_gb300/csrc/swcs_rowsweep.cuh"]),
+    "ansatz": ("profiles/ansatz_so52_e12_N1e6.md",
+               ["paper_2411_07920_gb300/csrc/swcs_ansatz.cu", "paper_2411_07920_gb300/csrc/swcs_select.cuh"]),
+}
+
+
+def source_sha16(paths):
+    """sha256 prefix of the concatenated sources of a kernel."""
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def measured_traffic(kernel, args):
     """DRAM bytes per launch of the dominant kernel from its committed ncu summary,
     only for the workload and launch shape that were captured and while the
     kernel's source is the one that was captured (else None)."""
-    import hashlib
-    files = {"row_sweep": ("profiles/row_sweep_so52_e12_N1e6.md", "paper_2411_07920_gb300/csrc/swcs_rowsweep.cu")}
-    if kernel not in files:
+    if kernel not in TRAFFIC_FILES:
         return None
     if args.sweep == 1 or any(getattr(args, k) != v for k, v in TRAFFIC_CAPTURED.items()):
         return None
-    summary, src = (os.path.join(ROOT, f) for f in files[kernel])
+    summary, srcs = TRAFFIC_FILES[kernel]
     try:
-        text = open(summary).read()
+        text = open(os.path.join(ROOT, summary)).read()
         want = text.split("source_sha256:")[1].split()[0]
         traffic = int(text.split("traffic_bytes_per_launch:")[1].split()[0])
-        have = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        have = source_sha16(srcs)
     except (OSError, IndexError, ValueError):
         return None
     return traffic if have == want else None

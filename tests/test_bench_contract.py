@@ -28,17 +28,19 @@ def test_reference_arm_prints_one_contract_line():
 
 
 def test_committed_traffic_is_reported_only_for_the_captured_launch():
-    """The ncu DRAM traffic in the row-sweep summary belongs to the default
-    workload and launch shape; any other bench configuration reports null."""
+    """The ncu DRAM traffic in the row-sweep and gate-kernel summaries belongs to
+    the default workload and launch shape; any other bench configuration
+    reports null."""
     sys.path.insert(0, ROOT)
     import bench
-    text = open(os.path.join(ROOT, "profiles", "row_sweep_so52_e12_N1e6.md")).read()
-    committed = int(text.split("traffic_bytes_per_launch:")[1].split()[0])
-    assert bench.measured_traffic("row_sweep", bench.parse([])) in (committed, None)
-    for argv in (["--n-keep", "300000"], ["--threads", "256"], ["--cluster", "1"], ["--row-occupancy", "3"],
-                 ["--rows-l2", "1"], ["--sweep", "1"]):
-        assert bench.measured_traffic("row_sweep", bench.parse(argv)) is None, argv
-    assert bench.measured_traffic("ansatz", bench.parse([])) is None
+    for kernel, name in (("row_sweep", "row_sweep_so52_e12_N1e6.md"), ("ansatz", "ansatz_so52_e12_N1e6.md")):
+        text = open(os.path.join(ROOT, "profiles", name)).read()
+        committed = int(text.split("traffic_bytes_per_launch:")[1].split()[0])
+        assert bench.measured_traffic(kernel, bench.parse([])) in (committed, None)
+        for argv in (["--n-keep", "300000"], ["--threads", "512"], ["--cluster", "2"], ["--rows-l2", "1"],
+                     ["--sweep", "1"]):
+            assert bench.measured_traffic(kernel, bench.parse(argv)) is None, argv
+    assert bench.measured_traffic("energy", bench.parse([])) is None
 
 
 def test_scaling_exponent_recovers_a_power_law():
