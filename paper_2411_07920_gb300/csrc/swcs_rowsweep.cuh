@@ -63,6 +63,7 @@ struct RowShared {
   long long gx_off, gx_cnt;  // the alpha group of X itself
   unsigned scan_tmp[kRowMaxWarps];
   double red[kRowMaxWarps];
+  unsigned next_item[3][2];  // per pass: the next alpha-beta item and alpha-double item to hand out
 };
 
 // Dynamic shared memory: entry lists, the staged share of the discovery, the
@@ -206,6 +207,13 @@ __device__ __forceinline__ int warp_find_entry(const RowEnt* ents, int cnt, uint
 // mark the row sectors that selected operators will read.
 enum RowPass { kPassScatter = 0, kPassGather = 1, kPassMark = 2 };
 
+// n work items from a counter in shared memory, for the whole warp (every lane must call it).
+__device__ __forceinline__ uint32_t take_items(unsigned* ctr, uint32_t n, int lane) {
+  uint32_t v = 0;
+  if (lane == 0) v = atomicAdd(ctr, n);
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+
 __device__ __forceinline__ void mark_sector(unsigned* touched, uint32_t i) {
   const unsigned bit = sector_bit(i);
   if (!(touched[sector_word(i)] & bit)) atomicOr(&touched[sector_word(i)], bit);
@@ -338,11 +346,16 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
   }
   // ---------------- alpha-single neighbours, the alpha single itself: one determinant per lane.  Each
   // lane sums its own Fock element h_qp + sum_{k in D} <qk||pk> (no warp reduction per determinant)
-  // items of the neighbour groups: split over the cluster when every CTA holds the target's whole lists,
-  // else each CTA works through the groups it found
+  // items of the neighbour groups: split over the cluster by a fixed stride when every CTA holds the
+  // target's whole lists; else each CTA works through the groups it found, its warps taking the items of
+  // the alpha-beta and alpha-double loops from counters in shared memory (a warp that finishes early takes
+  // more, which evens out the waits at the barrier after the pass)
   const bool merged = A.stage_ent_s > 0;
+  const bool dyn = !merged;
   const uint32_t gwarp = (uint32_t)((merged ? crank * kRowWarps : 0) + warp);
   const uint32_t gwarps = (uint32_t)((merged ? gsz : 1) * kRowWarps);
+  unsigned* const ctr_ab = &sh.next_item[PASS][0];
+  unsigned* const ctr_d = &sh.next_item[PASS][1];
   for (uint32_t t0 = gwarp * 32; t0 < sh.tot_s; t0 += gwarps * 32) {
     int e1 = warp_find_entry(dy.ents_s, sh.n_s, t0, lane);
     const int ej = e1 + lane;
@@ -395,8 +408,10 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
       wb_n[u] = t2 < nsb ? __ldg(&rb[t2]) : 0u;
     }
   };
-  if (gwarp < sh.tot_s) fetch(gwarp);
-  for (uint32_t t = gwarp; t < sh.tot_s; t += gwarps) {
+  uint32_t t = dyn ? take_items(ctr_ab, 1, lane) : gwarp;
+  if (t < sh.tot_s) fetch(t);
+  while (t < sh.tot_s) {
+    const uint32_t tn = dyn ? take_items(ctr_ab, 1, lane) : t + gwarps;  // this warp's next item
     const RowEnt en = dy.ents_s[e];
     const long long di = di_n;
     const uint64_t d = d_n;
@@ -404,7 +419,7 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
     uint32_t wb0[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) wb0[u] = wb_n[u];
-    if (t + gwarps < sh.tot_s) fetch(t + gwarps);
+    if (tn < sh.tot_s) fetch(tn);
     if (!packed) warp_lists(sh, warp, lane, d, m);  // unpacked entries: pair indices from the beta lists
     const int pa = en.o[0], pb = en.o[2];  // alpha spin-orbitals: removed, added
     // alpha-beta doubles: phase = (beta single on D) ^ (alpha single on D) ^ (index-only bit in the tables);
@@ -434,6 +449,7 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
         }
       }
       __syncwarp();
+      t = tn;
       continue;
     }
     for (int t0 = 0; t0 < nsb; t0 += 128) {
@@ -500,6 +516,7 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
       }
     }
     __syncwarp();
+    t = tn;
   }
   // ---------------- alpha-double neighbours: one determinant per lane; the warp finds the entry of
   // its first item, then each lane counts the entries that start at or before its own item (lane j
@@ -507,7 +524,8 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
   // so the starts are distinct and the walk below takes no step).  Every item of an entry is the same
   // pool operator, so the gather sums each entry's lanes in the warp and its first lane adds the total.
   const int npairs = A.H.npairs, n = A.H.n;
-  for (uint32_t t0 = gwarp * 32; t0 < sh.tot_d; t0 += gwarps * 32) {
+  for (uint32_t t0 = dyn ? take_items(ctr_d, 32, lane) : gwarp * 32; t0 < sh.tot_d;
+       t0 = dyn ? take_items(ctr_d, 32, lane) : t0 + gwarps * 32) {
     int e = warp_find_entry(dy.ents_d, sh.n_d, t0, lane);
     const int ej = e + lane;
     const uint32_t st = (lane > 0 && ej < sh.n_d) ? dy.ents_d[ej].flat - t0 : 32u;
@@ -750,6 +768,7 @@ __device__ void row_target(const RowArgs& A, RowShared& sh, const RowDyn& dy, do
       sh.n_d = min(bd, A.max_ent_d);
     }
   }
+  if (threadIdx.x < 6) (&sh.next_item[0][0])[threadIdx.x] = 0u;  // read only after the scans' barriers
   __syncthreads();
   scan_items<kRowThreads>(sh, dy.ents_s, sh.n_s, 1, &sh.tot_s);
   scan_items<kRowThreads>(sh, dy.ents_d, sh.n_d, kDblChunk, &sh.tot_d);
