@@ -281,7 +281,8 @@ __device__ void tile_row(const BatchInst& I, const BatchTask& k, unsigned char* 
   BlockSync sy;
   double e_acc = 0.0;
   unsigned n_lookups = 0, n_probe_slots = 0;
-  row_target<kRowThreads>(A, sh, dy, row, (int)k.tile, false, false, 0, 1, sy, e_acc, n_lookups, n_probe_slots);
+  row_target<kRowThreads>(A, sh, dy, row, (int)k.tile, false, false, 0, 1, sy, e_acc, n_lookups, n_probe_slots,
+                          false);  // the row is clean again for the next work item, whichever instance it belongs to
   row_flush<kRowThreads>(A, sh, e_acc, n_lookups, n_probe_slots);
 }
 

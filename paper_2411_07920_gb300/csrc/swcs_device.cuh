@@ -55,6 +55,22 @@ __device__ __forceinline__ int64_t idx_lookup(const IdxSlot* __restrict__ t, uin
   return -1;
 }
 
+// The lookup continued from slot s after n0 slots already visited; adds the slots it visited (the n0
+// included) to *probes when probes is given.
+__device__ __forceinline__ int64_t idx_lookup_at(const IdxSlot* __restrict__ t, uint64_t mask, uint64_t key, uint64_t s,
+                                                 uint64_t n0, unsigned* probes) {
+  for (uint64_t n = n0; n <= mask; ++n) {
+    const IdxSlot sl = t[s];
+    if (sl.key == key || sl.key == kEmpty) {
+      if (probes) *probes += (unsigned)n + 1u;
+      return sl.key == key ? (int64_t)sl.idx : -1;
+    }
+    s = (s + 1) & mask;
+  }
+  if (probes) *probes += (unsigned)(mask + 1);
+  return -1;
+}
+
 // The same lookup, also adding the number of slots it visited to *probes.
 __device__ __forceinline__ int64_t idx_lookup_counted(const IdxSlot* __restrict__ t, uint64_t mask, uint64_t key,
                                                       unsigned* probes) {

@@ -62,7 +62,7 @@ row_sweep_kernel(RowArgs A) {
   const int n_own = n_targets > sh0 ? (n_targets - sh0 + n_sh - 1) / n_sh : 0;
   for (int jx = cid; jx < n_own; jx += ncl)
     row_target<kRowThreads>(A, sh, dy, row, sh0 + jx * n_sh, probe, screen, crank, gsz, sy, e_acc, n_lookups,
-                            n_probe_slots);
+                            n_probe_slots, true);  // rows are zeroed before the launch, so a CTA's last clear can go
   row_flush<kRowThreads>(A, sh, e_acc, n_lookups, n_probe_slots);
 }
 

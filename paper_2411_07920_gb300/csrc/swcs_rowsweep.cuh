@@ -650,13 +650,42 @@ __device__ void row_cta_init(const RowArgs& A, RowShared& sh, const RowDyn& dy) 
   __syncthreads();
 }
 
+// Zeroes the row entries this CTA touched for its last target (each CTA clears its own sectors), or its
+// slice of the whole row when there is no touched bitmap.
+template <int kRowThreads>
+__device__ void row_clear(const RowArgs& A, const RowDyn& dy, double* row, int crank, int gsz) {
+  const int nwords = A.touched_words;
+  if (dy.touched) {  // clear the entries this CTA touched (others clear theirs)
+    for (int w = threadIdx.x; w < nwords; w += kRowThreads) {
+      unsigned bits = dy.touched[w];
+      if (!bits) continue;
+      dy.touched[w] = 0u;
+      while (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1u;
+        const int64_t e0 = ((int64_t)w * 32 + b) * 4;  // first entry of the sector
+        if (e0 + 3 < A.NB) {  // a whole sector in one 32-byte store: rows start on 32-byte boundaries
+          asm volatile("st.global.v4.b64 [%0], {%1, %1, %1, %1};" ::"l"(__cvta_generic_to_global(row + e0)), "l"(0ull)
+                       : "memory");
+        } else {
+          for (int64_t e = e0; e < A.NB; ++e) row[e] = 0.0;
+        }
+      }
+    }
+  } else {  // clear this CTA's slice of the row
+    const int64_t per = (A.NB + gsz - 1) / gsz;
+    const int64_t b = per * crank, e = (A.NB < b + per) ? A.NB : b + per;
+    for (int64_t i = b + threadIdx.x; i < e; i += kRowThreads) row[i] = 0.0;
+  }
+}
+
 // One target alpha string xi of the sweep: discovery of its neighbour groups,
 // scatter, gather (or the energy / probe read-back), clear.  Every CTA of the
 // target's group calls it with the same xi.
 template <int kRowThreads, class Sync>
 __device__ void row_target(const RowArgs& A, RowShared& sh, const RowDyn& dy, double* row, int xi, bool probe,
                            bool screen, int crank, int gsz, Sync& sy, double& e_acc, unsigned& n_lookups,
-                           unsigned& n_probe_slots) {
+                           unsigned& n_probe_slots, bool defer_clear) {
   const int m = A.H.n >> 1, ks = A.H.no, nvs = A.H.nv;
   const int n_to = ks * (ks - 1) / 2, n_tv = nvs * (nvs - 1) / 2;
   const int ns = ks * nvs, nd = n_to * n_tv;
@@ -683,7 +712,77 @@ __device__ void row_target(const RowArgs& A, RowShared& sh, const RowDyn& dy, do
   }
   __syncthreads();
   if (A.energy_only && sh.gx_cnt == 0) return;  // same decision in every CTA of the cluster
-  if (A.energy_only && dy.touched) {  // the entries that will be read back: X's own determinants
+  // Candidates c = 0 .. ns+nd-1 (alpha singles then doubles of X); this CTA takes c = crank (mod gsz), each
+  // thread up to kDisc at a time with their home slots read together.  A clear of the previous target that
+  // was deferred to here runs while those reads are in flight.
+  constexpr int kDisc = 3;
+  const int n_cand = ns + nd;
+  for (int r = 0;; ++r) {
+    const int cb = (int)threadIdx.x + r * kDisc * kRowThreads;
+    if (r > 0 && crank + cb * gsz >= n_cand) break;
+    uint32_t Yk[kDisc], ok4[kDisc];
+    IdxSlot sl[kDisc];
+#pragma unroll
+    for (int k = 0; k < kDisc; ++k) {
+      const int c = crank + (cb + k * kRowThreads) * gsz;
+      Yk[k] = 0u;
+      ok4[k] = 0u;
+      sl[k].key = kEmpty;
+      sl[k].idx = 0;
+      if (c >= n_cand) continue;
+      uint32_t Y;
+      uint8_t o4[4];
+      if (c < ns) {
+        const int b = sh.occx[c / nvs], a = sh.virx[c % nvs];
+        Y = X ^ (1u << b) ^ (1u << a);
+        o4[0] = (uint8_t)(2 * a); o4[1] = 0; o4[2] = (uint8_t)(2 * b); o4[3] = 0;
+      } else {
+        const int dd = c - ns;
+        const uint16_t oo = sh.tri_o[dd / n_tv], vv = sh.tri_v[dd % n_tv];
+        const int b1 = sh.occx[oo & 255], b2 = sh.occx[oo >> 8];
+        const int a1 = sh.virx[vv & 255], a2 = sh.virx[vv >> 8];
+        Y = X ^ (1u << b1) ^ (1u << b2) ^ (1u << a1) ^ (1u << a2);
+        o4[0] = (uint8_t)(2 * a1); o4[1] = (uint8_t)(2 * a2); o4[2] = (uint8_t)(2 * b1); o4[3] = (uint8_t)(2 * b2);
+      }
+      Yk[k] = Y;
+      ok4[k] = (uint32_t)o4[0] | ((uint32_t)o4[1] << 8) | ((uint32_t)o4[2] << 16) | ((uint32_t)o4[3] << 24);
+      sl[k] = A.atab[mix64((uint64_t)Y) & A.amask];
+    }
+    if (r == 0 && defer_clear) row_clear<kRowThreads>(A, dy, row, crank, gsz);
+#pragma unroll
+    for (int k = 0; k < kDisc; ++k) {
+      const int c = crank + (cb + k * kRowThreads) * gsz;
+      if (c >= n_cand) continue;
+      const uint64_t Y = Yk[k];
+      int64_t g;
+      unsigned* pc = A.probe_ctr ? &n_probe_slots : nullptr;
+      if (sl[k].key == Y || sl[k].key == kEmpty) {
+        g = sl[k].key == Y ? (int64_t)sl[k].idx : -1;
+        if (pc) *pc += 1u;
+      } else {
+        g = idx_lookup_at(A.atab, A.amask, Y, (mix64(Y) + 1) & A.amask, 1, pc);
+      }
+      if (A.probe_ctr) ++n_lookups;
+      if (g >= 0) {
+        RowEnt en;
+        en.off = (uint32_t)A.goff[g];
+        en.flat = (uint32_t)(A.goff[g + 1] - A.goff[g]);
+        en.o[0] = (uint8_t)ok4[k]; en.o[1] = (uint8_t)(ok4[k] >> 8);
+        en.o[2] = (uint8_t)(ok4[k] >> 16); en.o[3] = (uint8_t)(ok4[k] >> 24);
+        const int cap_s = merged ? A.stage_ent_s : A.max_ent_s, cap_d = merged ? A.stage_ent_d : A.max_ent_d;
+        if (c < ns) {
+          const int slot = atomicAdd(&sh.n_s_loc, 1);
+          if (slot < cap_s) dy.stage_s[slot] = en;
+        } else {
+          const int slot = atomicAdd(&sh.n_d_loc, 1);
+          if (slot < cap_d) dy.stage_d[slot] = en;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // the entries that will be read back (after this CTA's clear of the previous target's sectors)
+  if (A.energy_only && dy.touched) {  // X's own determinants
     for (long long t = threadIdx.x; t < sh.gx_cnt; t += kRowThreads) {
       const uint32_t rk = __ldg(&A.grank[sh.gx_off + t]);
       atomicOr(&dy.touched[sector_word(rk)], sector_bit(rk));
@@ -695,47 +794,6 @@ __device__ void row_target(const RowArgs& A, RowShared& sh, const RowDyn& dy, do
       atomicOr(&dy.touched[sector_word(rk)], sector_bit(rk));
     }
   }
-  // candidates c = 0 .. ns+nd-1 (alpha singles then doubles of X); this CTA takes c = crank (mod gsz)
-  for (int cc = threadIdx.x; crank + cc * gsz < ns + nd; cc += kRowThreads) {
-    const int c = crank + cc * gsz;
-    uint32_t Y;
-    uint8_t o4[4];
-    const bool single = c < ns;
-    if (single) {
-      const int b = sh.occx[c / nvs], a = sh.virx[c % nvs];
-      Y = X ^ (1u << b) ^ (1u << a);
-      o4[0] = (uint8_t)(2 * a); o4[1] = 0; o4[2] = (uint8_t)(2 * b); o4[3] = 0;
-    } else {
-      const int dd = c - ns;
-      const uint16_t oo = sh.tri_o[dd / n_tv], vv = sh.tri_v[dd % n_tv];
-      const int b1 = sh.occx[oo & 255], b2 = sh.occx[oo >> 8];
-      const int a1 = sh.virx[vv & 255], a2 = sh.virx[vv >> 8];
-      Y = X ^ (1u << b1) ^ (1u << b2) ^ (1u << a1) ^ (1u << a2);
-      o4[0] = (uint8_t)(2 * a1); o4[1] = (uint8_t)(2 * a2); o4[2] = (uint8_t)(2 * b1); o4[3] = (uint8_t)(2 * b2);
-    }
-    int64_t g;
-    if (A.probe_ctr) {
-      g = idx_lookup_counted(A.atab, A.amask, (uint64_t)Y, &n_probe_slots);
-      ++n_lookups;
-    } else {
-      g = idx_lookup(A.atab, A.amask, (uint64_t)Y);
-    }
-    if (g >= 0) {
-      RowEnt en;
-      en.off = (uint32_t)A.goff[g];
-      en.flat = (uint32_t)(A.goff[g + 1] - A.goff[g]);
-      en.o[0] = o4[0]; en.o[1] = o4[1]; en.o[2] = o4[2]; en.o[3] = o4[3];
-      const int cap_s = merged ? A.stage_ent_s : A.max_ent_s, cap_d = merged ? A.stage_ent_d : A.max_ent_d;
-      if (single) {
-        const int slot = atomicAdd(&sh.n_s_loc, 1);
-        if (slot < cap_s) dy.stage_s[slot] = en;
-      } else {
-        const int slot = atomicAdd(&sh.n_d_loc, 1);
-        if (slot < cap_d) dy.stage_d[slot] = en;
-      }
-    }
-  }
-  __syncthreads();
   if (threadIdx.x == 0) {
     const int cap_s = merged ? A.stage_ent_s : A.max_ent_s, cap_d = merged ? A.stage_ent_d : A.max_ent_d;
     if (sh.n_s_loc > cap_s || sh.n_d_loc > cap_d) set_error(A.err, kDevBadState);
@@ -804,28 +862,7 @@ __device__ void row_target(const RowArgs& A, RowShared& sh, const RowDyn& dy, do
     row_phase<kRowThreads, kPassGather>(A, sh, dy, row, crank, gsz, e_acc);
   }
   sy.sync();
-  if (dy.touched) {  // clear the entries this CTA touched (others clear theirs)
-    for (int w = threadIdx.x; w < nwords; w += kRowThreads) {
-      unsigned bits = dy.touched[w];
-      if (!bits) continue;
-      dy.touched[w] = 0u;
-      while (bits) {
-        const int b = __ffs(bits) - 1;
-        bits &= bits - 1u;
-        const int64_t e0 = ((int64_t)w * 32 + b) * 4;  // first entry of the sector
-        if (e0 + 3 < A.NB) {  // a whole sector: rows start on 32-byte boundaries
-          reinterpret_cast<double2*>(row + e0)[0] = make_double2(0.0, 0.0);
-          reinterpret_cast<double2*>(row + e0)[1] = make_double2(0.0, 0.0);
-        } else {
-          for (int64_t e = e0; e < A.NB; ++e) row[e] = 0.0;
-        }
-      }
-    }
-  } else {  // clear this CTA's slice of the row
-    const int64_t per = (A.NB + gsz - 1) / gsz;
-    const int64_t b = per * crank, e = (A.NB < b + per) ? A.NB : b + per;
-    for (int64_t i = b + threadIdx.x; i < e; i += kRowThreads) row[i] = 0.0;
-  }
+  if (!defer_clear) row_clear<kRowThreads>(A, dy, row, crank, gsz);
 }
 
 // End of a CTA's sweep: hash-probe counters and its part of the energy numerator.
