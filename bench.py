@@ -587,6 +587,22 @@ def run_screen_leg(swcs, ctx, w, args, torch, frac=0.05):
     except Exception:
         pass
     bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    # one training step (five tensor-core GEMMs, transposes, reductions, Adam) on the training batch and on a
+    # larger one, device time; the learning rate is 0 here, the network has served its purpose
+    step_ms = {}
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for nb in (8192, 65536):
+        if X.shape[0] < nb:
+            continue
+        xb, tb = X[:nb].contiguous(), T[:nb].contiguous()
+        net.train_step_dev(xb, tb, 0.0, loss)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(20):
+            net.train_step_dev(xb, tb, 0.0, loss)
+        e1.record(st)
+        e1.synchronize()
+        step_ms[str(nb)] = round(e0.elapsed_time(e1) / 20, 4)
     net.close()
     return {"frac": frac, "subset": best["subset"], "pool": best["pool"], "recall_argmax": best["recall_argmax"],
             "recall_top10": best["recall_top10"], "same_argmax": bool(best["same_argmax"]),
@@ -594,6 +610,7 @@ def run_screen_leg(swcs, ctx, w, args, torch, frac=0.05):
             "screened_ms": round(1e3 * best["t_screened"], 3), "speedup": round(best["speedup"], 3),
             "screened_sigma_in_full_ms": round(1e3 * t_sigma_full, 3),
             "train_s": round(t_train, 2), "train_samples": int(X.shape[0]), "train_loss": hist[-1][1],
+            "train_step_ms": step_ms,
             "mlp_forward": {"kernel": "mlp_fused_kernel", "ms": round(1e3 * t_fwd, 4),
                             "tflops": round(flops / t_fwd / 1e12, 2),
                             "frac_of_bf16_peak": round(flops / t_fwd / 1e12 / bf16_peak, 4),

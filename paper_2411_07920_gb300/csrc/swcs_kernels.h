@@ -311,6 +311,11 @@ struct MlpParams {
   __nv_bfloat16* w3b;
 };
 cudaError_t launch_mlp_gemm(const GemmArgs& g, cudaStream_t st);
+// Pipelined form with tensor maps of A ([M x K], boxes of 8 x 128) and B ([N x K], boxes of 8 x N); splits > 1
+// (kGemmF32 only) adds partial products into out_f32, which must hold zeros.
+cudaError_t launch_mlp_gemm_tma(const CUtensorMap& tm_a, const CUtensorMap& tm_b, const GemmArgs& g, int splits,
+                                cudaStream_t st);
+int mlp_gemm_tma_kc(int K);
 // The w3 dot product of the last layer is summed as kDotGroups partial sums over
 // consecutive 16-column chunks (chunk c of n belongs to group g when
 // dot_group_begin(g, n) <= c < dot_group_begin(g + 1, n)), combined as

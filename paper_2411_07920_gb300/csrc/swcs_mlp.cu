@@ -23,7 +23,18 @@
 // gradients dW2 = dZ2^T H1, dW1 = dZ1^T X as GEMMs over the batch with
 // transposed operands.  Adam updates FP32 master weights and refreshes the
 // BF16 copies.
+//
+// With tensor maps for A and B (every shape the training step uses) the GEMM
+// runs pipelined instead (mlp_gemm_tma_kernel): warp 0 (one thread) streams
+// K-chunks of A and B into a ring of three shared-memory stages by TMA, warp 1
+// (one thread) issues the MMAs of each chunk as soon as it has landed and
+// frees the stage with a tcgen05.commit, so copies and MMAs overlap; the
+// weight-gradient GEMMs, which have only two 128-row tiles but a long K (the
+// batch), also split K over CTAs that add their partial products into the
+// zeroed FP32 output.
+#include <algorithm>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -197,6 +208,160 @@ __global__ void __launch_bounds__(kGemmThreads) mlp_gemm_kernel(GemmArgs g) {
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
 }
 
+// ---------------------------------------------------------------- pipelined GEMM (TMA + tcgen05)
+constexpr int kStages = 3;
+
+__device__ __forceinline__ void mbar_init1(uint64_t* b) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(b)));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(b))
+               : "memory");
+}
+// 2-D tile load: box origin (x = K element, y = row) into shared memory, completion on mbar.
+__device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(mbar))
+      : "memory");
+}
+
+// C = A B^T for one 128-row tile and K-chunks [c0, c1) of kc elements (this CTA's split of K).  Stage s
+// holds A as kc/8 column blocks of 128 rows x 16 B (one TMA box each: LBO 2 KB, SBO 128 B) and B as kc/8
+// blocks of N x 16 B (LBO N x 16 B, SBO 128 B).
+__global__ void __launch_bounds__(kGemmThreads)
+mlp_gemm_tma_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b, GemmArgs g,
+                    int kc, int splits) {
+  extern __shared__ __align__(128) uint8_t dsm[];
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], fin;
+  __shared__ uint32_t tmem_holder;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * 128;
+  const int ncols = g.N <= 32 ? 32 : (g.N <= 64 ? 64 : (g.N <= 128 ? 128 : 256));
+  const int nch = g.K / kc, per = (nch + splits - 1) / splits;
+  const int c0 = (int)blockIdx.y * per, c1 = min(nch, c0 + per);
+  const uint32_t a_bytes = 128u * (uint32_t)kc * 2u, b_bytes = (uint32_t)g.N * (uint32_t)kc * 2u;
+  uint8_t* stage[kStages];
+#pragma unroll
+  for (int s = 0; s < kStages; ++s) stage[s] = dsm + (size_t)s * (a_bytes + b_bytes);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 32) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init1(&full[s]);
+      mbar_init1(&empty[s]);
+    }
+    mbar_init1(&fin);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_holder;
+  const uint32_t idesc = idesc_bf16(128, g.N);
+  bool bad = false;
+  if (threadIdx.x == 0) {  // ------------------------------------------------ TMA producer
+    bool issued[kStages] = {};
+    uint32_t last[kStages] = {};
+    for (int c = c0; c < c1; ++c) {
+      const int j = c - c0, s = j % kStages;
+      const uint32_t par = (uint32_t)(j / kStages) & 1u;
+      if (!mbar_wait(smem_u32(&empty[s]), par ^ 1u)) {  // the MMAs that read this stage last have completed
+        bad = true;
+        break;
+      }
+      mbar_expect_tx(&full[s], a_bytes + b_bytes);
+      for (int q = 0; q < kc / 8; ++q) {
+        tma_2d(stage[s] + (size_t)q * 2048, &tm_a, c * kc + 8 * q, m0, &full[s]);
+        tma_2d(stage[s] + a_bytes + (size_t)q * g.N * 16, &tm_b, c * kc + 8 * q, 0, &full[s]);
+      }
+      issued[s] = true;
+      last[s] = par;
+    }
+    // no copy may still be landing when the CTA leaves (returns at once when already consumed)
+    for (int s = 0; s < kStages; ++s)
+      if (issued[s] && !mbar_wait(smem_u32(&full[s]), last[s])) bad = true;
+  } else if (threadIdx.x == 32) {  // ---------------------------------------- MMA issuer
+    for (int c = c0; c < c1 && !bad; ++c) {
+      const int j = c - c0, s = j % kStages;
+      if (!mbar_wait(smem_u32(&full[s]), (uint32_t)(j / kStages) & 1u)) {
+        bad = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int k = 0; k < kc / 16; ++k) {
+        const uint64_t da = smem_desc(smem_u32(stage[s]) + (uint32_t)k * 2 * 2048, 2048, 128);
+        const uint64_t db = smem_desc(smem_u32(stage[s] + a_bytes) + (uint32_t)k * 2 * g.N * 16, (uint32_t)g.N * 16, 128);
+        const uint32_t acc = (j > 0 || k > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc));
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(&fin);  // every MMA issued above has completed once this phase completes
+  }
+  __syncwarp();
+  if (!mbar_wait(smem_u32(&fin), 0)) bad = true;
+  bad = __syncthreads_or(bad) != 0;  // one decision for the whole CTA before the warp-wide tensor-memory loads
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // ---------------- epilogue: thread t owns row m0 + t (TMEM lane t)
+  const int row = m0 + threadIdx.x;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;  // dot-product partial sums (kDotGroups)
+  const bool empty_split = c0 >= c1;               // no chunk: nothing was accumulated
+  if (!bad && !empty_split) {
+    for (int cc = 0; cc < g.N; cc += 16) {
+      float v[16];
+      tmem_ld16(tmem + lane_base + (uint32_t)cc, v);
+      int grp = 0;
+      while (grp < kDotGroups - 1 && dot_group_begin(grp + 1, g.N / 16) <= cc / 16) ++grp;
+      float part = grp == 0 ? p0 : (grp == 1 ? p1 : (grp == 2 ? p2 : p3));
+      if (row < g.M) {
+        if (g.mode == kGemmF32) {
+          float* o = g.out_f32 + (size_t)row * g.ldo + cc;
+          if (splits > 1) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) atomicAdd(&o[i], v[i]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) o[i] = v[i];
+          }
+        } else {
+          __nv_bfloat16* o = g.out_bf16 + (size_t)row * g.ldo + cc;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            float z = v[i] + (g.bias ? g.bias[cc + i] : 0.f);
+            z = z > 0.f ? z : 0.f;
+            const __nv_bfloat16 hb = __float2bfloat16_rn(z);
+            o[i] = hb;
+            if (g.mode == kGemmReluBf16Dot) part += __bfloat162float(hb) * __bfloat162float(g.w3[cc + i]);
+          }
+        }
+      }
+      if (grp == 0) p0 = part;
+      else if (grp == 1) p1 = part;
+      else if (grp == 2) p2 = part;
+      else p3 = part;
+    }
+  }
+  if (g.mode == kGemmReluBf16Dot && row < g.M && !bad) g.y[row] = (((p0 + p1) + p2) + p3) + g.b3;
+  if (bad && g.err) set_error(g.err, kDevTimeout);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+}
+
 // ---------------------------------------------------------------- elementwise / reductions
 __global__ void mlp_dy_kernel(const float* y, const float* t, int B, float* dy, double* loss) {
   double s = 0.0;
@@ -302,6 +467,28 @@ cudaError_t launch_mlp_gemm(const GemmArgs& g, cudaStream_t st) {
     attr_set = true;
   }
   mlp_gemm_kernel<<<(g.M + 127) / 128, kGemmThreads, kGemmReserveSmem, st>>>(g);
+  return cudaGetLastError();
+}
+
+// K-chunk of the pipelined GEMM: 64 where K allows, else 32.
+int mlp_gemm_tma_kc(int K) { return K % 64 == 0 ? 64 : 32; }
+
+cudaError_t launch_mlp_gemm_tma(const CUtensorMap& tm_a, const CUtensorMap& tm_b, const GemmArgs& g, int splits,
+                                cudaStream_t st) {
+  if (g.M <= 0 || g.N < 16 || g.N > 256 || (g.N & 15) || g.K <= 0 || (g.K % kKChunk) || splits < 1 ||
+      (splits > 1 && g.mode != kGemmF32))
+    return cudaErrorInvalidValue;
+  const int kc = mlp_gemm_tma_kc(g.K);
+  const size_t stage = (size_t)128 * kc * 2 + (size_t)g.N * kc * 2;
+  // at most two CTAs per SM, so their tensor-memory columns (<= 256 each) never oversubscribe the 512
+  const size_t smem = std::max((size_t)kStages * stage, (size_t)kGemmReserveSmem);
+  static size_t attr = 0;
+  if (attr < smem) {
+    const cudaError_t e = cudaFuncSetAttribute(mlp_gemm_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = smem;
+  }
+  mlp_gemm_tma_kernel<<<dim3((g.M + 127) / 128, splits), kGemmThreads, smem, st>>>(tm_a, tm_b, g, kc, splits);
   return cudaGetLastError();
 }
 

@@ -1,4 +1,5 @@
 // Host side of the screening network (swcs_mlp_* in include/swcs.h).
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -87,6 +88,29 @@ GemmArgs gemm(swcs_mlp* m, const __nv_bfloat16* A, int lda, const __nv_bfloat16*
   return g;
 }
 
+bool k_major_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_t rows, uint32_t box_rows);
+
+// C = A B^T through the pipelined kernel when both operands have tensor maps (K contiguous, 16-byte aligned),
+// else through the staged one.  may_split: the FP32 output holds zeros, so K may be split over CTAs.
+int run_gemm(swcs_mlp* m, const GemmArgs& g, bool may_split) {
+  CUtensorMap ta, tb;
+  if (g.lda == g.K && g.ldb == g.K && k_major_map(&ta, g.A, (uint64_t)g.K, (uint64_t)g.M, 128) &&
+      k_major_map(&tb, g.B, (uint64_t)g.K, (uint64_t)g.N, (uint32_t)g.N)) {
+    int splits = 1;
+    if (may_split && g.mode == kGemmF32) {
+      int dev = 0, nsm = 0;
+      MCK(cudaGetDevice(&dev));
+      MCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+      const int tiles = (g.M + 127) / 128, nch = g.K / mlp_gemm_tma_kc(g.K);
+      splits = std::max(1, std::min(nch / 4, (2 * nsm) / tiles));  // at least four K-chunks per CTA
+    }
+    MCK(launch_mlp_gemm_tma(ta, tb, g, splits, m->st));
+  } else {
+    MCK(launch_mlp_gemm(g, m->st));
+  }
+  return SWCS_OK;
+}
+
 // forward into m->H1, m->H2, y
 int forward(swcs_mlp* m, const __nv_bfloat16* x, int64_t n, float* y) {
   const int W = m->p.width, D = m->p.d_in;
@@ -94,7 +118,8 @@ int forward(swcs_mlp* m, const __nv_bfloat16* x, int64_t n, float* y) {
   g1.bias = m->p.master + m->p.off_b1;
   g1.out_bf16 = m->H1;
   g1.ldo = W;
-  MCK(launch_mlp_gemm(g1, m->st));
+  int r;
+  if ((r = run_gemm(m, g1, false))) return r;
   GemmArgs g2 = gemm(m, m->H1, W, m->p.W2b, W, (int)n, W, W, kGemmReluBf16Dot);
   g2.bias = m->p.master + m->p.off_b2;
   g2.out_bf16 = m->H2;
@@ -103,7 +128,7 @@ int forward(swcs_mlp* m, const __nv_bfloat16* x, int64_t n, float* y) {
   // b3 is read on the device side through the bias of a 1-column add: kept on host copy
   g2.b3 = 0.f;
   g2.y = y;
-  MCK(launch_mlp_gemm(g2, m->st));
+  if ((r = run_gemm(m, g2, false))) return r;
   m->launches += 2;
   return SWCS_OK;
 }
@@ -192,7 +217,7 @@ int grads(swcs_mlp* m, const __nv_bfloat16* x, const float* t, int64_t n, double
   GemmArgs g3 = gemm(m, m->dZ2, W, m->p.W2tb, W, (int)n, W, W, kGemmF32);  // dH1 = dZ2 W2
   g3.out_f32 = m->dH1;
   g3.ldo = W;
-  MCK(launch_mlp_gemm(g3, m->st));
+  if ((r = run_gemm(m, g3, false))) return r;
   MCK(launch_mlp_dz1(m->dH1, m->H1, (size_t)n * W, m->dZ1, m->st));
   MCK(launch_mlp_colsum(m->dZ2, (int)n, W, m->grad + m->p.off_b2, m->st));
   MCK(launch_mlp_colsum(m->dZ1, (int)n, W, m->grad + m->p.off_b1, m->st));
@@ -203,11 +228,11 @@ int grads(swcs_mlp* m, const __nv_bfloat16* x, const float* t, int64_t n, double
   GemmArgs g4 = gemm(m, m->dZ2t, Bpad, m->H1t, Bpad, W, W, Bpad, kGemmF32);  // dW2 = dZ2^T H1
   g4.out_f32 = m->grad + m->p.off_W2;
   g4.ldo = W;
-  MCK(launch_mlp_gemm(g4, m->st));
+  if ((r = run_gemm(m, g4, true))) return r;  // into the zeroed gradient
   GemmArgs g5 = gemm(m, m->dZ1t, Bpad, m->Xt, Bpad, W, D, Bpad, kGemmF32);  // dW1 = dZ1^T X
   g5.out_f32 = m->grad + m->p.off_W1;
   g5.ldo = D;
-  MCK(launch_mlp_gemm(g5, m->st));
+  if ((r = run_gemm(m, g5, true))) return r;
   m->launches += 12;
   if (d_loss) MCK(cudaMemcpyAsync(d_loss, m->loss, sizeof(double), cudaMemcpyDeviceToDevice, m->st));
   return SWCS_OK;
