@@ -223,9 +223,11 @@ __device__ __forceinline__ bool selected(const RowArgs& A, int k) {
   return !A.sel_bits || ((__ldg(&A.sel_bits[k >> 5]) >> (k & 31)) & 1u);
 }
 
+// items: the counters that hand out the alpha-beta and alpha-double work items of each pass (next_item of
+// this CTA, or of the cluster's first CTA when the cluster shares the target's lists).
 template <int kRowThreads, int PASS>
 __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, double* row, int crank, int gsz,
-                          double& e_acc) {
+                          double& e_acc, unsigned* items) {
   constexpr bool SCATTER = PASS == kPassScatter;
   constexpr bool MARK = PASS == kPassMark;
   constexpr int kRowWarps = kRowThreads / 32;
@@ -346,16 +348,17 @@ __device__ void row_phase(const RowArgs& A, RowShared& sh, const RowDyn& dy, dou
   }
   // ---------------- alpha-single neighbours, the alpha single itself: one determinant per lane.  Each
   // lane sums its own Fock element h_qp + sum_{k in D} <qk||pk> (no warp reduction per determinant)
-  // items of the neighbour groups: split over the cluster by a fixed stride when every CTA holds the
-  // target's whole lists; else each CTA works through the groups it found, its warps taking the items of
-  // the alpha-beta and alpha-double loops from counters in shared memory (a warp that finishes early takes
-  // more, which evens out the waits at the barrier after the pass)
+  // items of the neighbour groups: the alpha singles split by a fixed stride (over the cluster when every
+  // CTA holds the target's whole lists, else within the CTA over the groups it found); the warps take the
+  // items of the alpha-beta and alpha-double loops from shared counters (in the cluster's first CTA when
+  // the lists are shared), so a warp that finishes early takes more and the waits at the barrier after the
+  // pass stay short
   const bool merged = A.stage_ent_s > 0;
-  const bool dyn = !merged;
+  const bool dyn = true;
   const uint32_t gwarp = (uint32_t)((merged ? crank * kRowWarps : 0) + warp);
   const uint32_t gwarps = (uint32_t)((merged ? gsz : 1) * kRowWarps);
-  unsigned* const ctr_ab = &sh.next_item[PASS][0];
-  unsigned* const ctr_d = &sh.next_item[PASS][1];
+  unsigned* const ctr_ab = items + 2 * PASS;
+  unsigned* const ctr_d = items + 2 * PASS + 1;
   for (uint32_t t0 = gwarp * 32; t0 < sh.tot_s; t0 += gwarps * 32) {
     int e1 = warp_find_entry(dy.ents_s, sh.n_s, t0, lane);
     const int ej = e1 + lane;
@@ -702,6 +705,7 @@ __device__ void row_target(const RowArgs& A, RowShared& sh, const RowDyn& dy, do
     const unsigned below = (1u << lane) - 1u;
     if (o) sh.occx[__popc(bo & below)] = (uint8_t)lane;
     else if (inr) sh.virx[__popc(bv & below)] = (uint8_t)lane;
+    if (lane < 6) (&sh.next_item[0][0])[lane] = 0u;  // every CTA of the cluster is past the last target's passes
     if (lane == 0) {
       sh.n_s_loc = 0;
       sh.n_d_loc = 0;
@@ -826,16 +830,16 @@ __device__ void row_target(const RowArgs& A, RowShared& sh, const RowDyn& dy, do
       sh.n_d = min(bd, A.max_ent_d);
     }
   }
-  if (threadIdx.x < 6) (&sh.next_item[0][0])[threadIdx.x] = 0u;  // read only after the scans' barriers
   __syncthreads();
   scan_items<kRowThreads>(sh, dy.ents_s, sh.n_s, 1, &sh.tot_s);
   scan_items<kRowThreads>(sh, dy.ents_d, sh.n_d, kDblChunk, &sh.tot_d);
+  unsigned* items = merged ? sy.remote(&sh.next_item[0][0], 0) : &sh.next_item[0][0];
 
   if (screen) {
     // the sectors the selected operators read (and the state's own determinants, for the energy),
     // marked by every CTA for its share of the pairs, then merged over the cluster
     for (long long t = threadIdx.x; t < sh.gx_cnt; t += kRowThreads) mark_sector(dy.touched, __ldg(&A.grank[sh.gx_off + t]));
-    row_phase<kRowThreads, kPassMark>(A, sh, dy, row, crank, gsz, e_acc);
+    row_phase<kRowThreads, kPassMark>(A, sh, dy, row, crank, gsz, e_acc, items);
     sy.sync();  // every CTA's marks are complete
     for (int w = threadIdx.x; w < nwords; w += kRowThreads) {
       unsigned bits = 0u;
@@ -845,7 +849,7 @@ __device__ void row_target(const RowArgs& A, RowShared& sh, const RowDyn& dy, do
     }
     __syncthreads();
   }
-  row_phase<kRowThreads, kPassScatter>(A, sh, dy, row, crank, gsz, e_acc);
+  row_phase<kRowThreads, kPassScatter>(A, sh, dy, row, crank, gsz, e_acc, items);
   sy.sync();
   if (probe) {  // the requested entries, split over the cluster
     const int t0 = __ldg(&A.probe_off[xi]), t1 = __ldg(&A.probe_off[xi + 1]);
@@ -859,7 +863,7 @@ __device__ void row_target(const RowArgs& A, RowShared& sh, const RowDyn& dy, do
       if (A.sig_out) A.sig_out[A.gorig[di]] = sg;
     }
   } else {
-    row_phase<kRowThreads, kPassGather>(A, sh, dy, row, crank, gsz, e_acc);
+    row_phase<kRowThreads, kPassGather>(A, sh, dy, row, crank, gsz, e_acc, items);
   }
   sy.sync();
   if (!defer_clear) row_clear<kRowThreads>(A, dy, row, crank, gsz);
