@@ -54,7 +54,8 @@ def parse(argv=None):
     p.add_argument("--threads", type=int, default=1024, help="threads per CTA of the row sweep")
     p.add_argument("--row-clusters", type=int, default=0, help="clusters of the row sweep (0: as many as fit)")
     p.add_argument("--row-occupancy", type=int, default=2, help="resident 512-thread row-sweep CTAs per SM (1, 2 or 3)")
-    p.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched leg")
+    p.add_argument("--no-batch", action="store_true",
+                   help="skip the 64-instance batched leg and the small configurations on the device")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     p.add_argument("--no-screen", action="store_true", help="skip the learned-screening leg")
     p.add_argument("--no-adapt", action="store_true", help="skip the ADAPT-VQE leg")
@@ -454,6 +455,11 @@ def run_swcs(args):
     if not args.no_screen:
         screen_res = run_screen_leg(swcs, ctx, w, args, torch)
 
+    # ------------------------------------------------------------ the two small configurations
+    configs = None
+    if not args.no_batch:
+        configs = run_configs_leg(swcs, I, torch)
+
     # ------------------------------------------------------------ batched leg: 64 uneven instances
     batch = None
     if not args.no_batch:
@@ -478,7 +484,7 @@ def run_swcs(args):
                 "gate_dets_per_s": gate_dets_per_s, "roofline": roof, "rooflines": rooflines, "cpu_baseline": cpu,
                 "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "energy_ms": round(min(energy_ms), 3), "hash_probes": probes,
-                "adjoint": adjoint, "batch": batch, "screen": screen_res, "adapt": adapt_res,
+                "adjoint": adjoint, "batch": batch, "screen": screen_res, "adapt": adapt_res, "configs": configs,
                 "kernels_ms": {k: round(v[0], 3) for k, v in prof.items()},
                 "ext": {"distinct": stats["ext_distinct"], "buckets": stats["ext_buckets"],
                         "capacity": stats["ext_capacity"]}}
@@ -643,6 +649,37 @@ def run_adapt_leg(swcs, w, args, torch):
            "grad_norms": [float(it.grad_norm) for it in a.history]}
     c.close()
     return res
+
+
+def run_configs_leg(swcs, I, torch, reps=5):
+    """The two small configurations on the device: one step (apply the ansatz, pool sweep) with inputs resident,
+    event-timed, with the energy and the state size."""
+    out = {}
+    for name in ("so12_e4", "so28_e8"):
+        w = I.workload(name)
+        with swcs.Context() as c:
+            c.load_hamiltonian(w.h, w.g, w.n_so, w.n_e)
+            d_ops = torch.from_numpy(w.ops.reshape(-1).copy()).cuda()
+            d_th = torch.from_numpy(w.theta.copy()).cuda()
+            d_g = torch.empty(c.pool_size(), dtype=torch.float64, device="cuda")
+            st = torch.cuda.current_stream()
+
+            def step():
+                c.apply_ansatz_dev(d_ops, d_th, w.n_keep)
+                c.pool_gradients_dev(d_g)
+            for _ in range(3):
+                step()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(reps):
+                step()
+            e1.record(st)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            e, _ = c.sweep_energy()
+            out[name] = {"step_ms": round(ms, 4), "sweeps_per_s": round(1e3 / ms, 2), "energy": e,
+                         "dets": int(len(c.get_state()[0])), "pool": int(c.pool_size())}
+    return out
 
 
 def run_batch_leg(swcs, I, torch, n_inst=64, seed0=100, reps=3):
