@@ -121,6 +121,7 @@ struct Ctrl {
   unsigned long long n_distinct;
   double ovl[3];  // swcs_overlap: <state|given>, <given|given>, <state|state>
   unsigned long long probes[4];  // hash probes: gate lookups, their slots, row-sweep lookups, their slots
+  unsigned row_next;  // the row sweep's next target
 };
 
 int fail(swcs_ctx* c, int code, const char* fmt, ...) {
@@ -644,6 +645,8 @@ int sweep_rows(swcs_ctx* c, double* d_g, int64_t nd_bound = -1, bool enqueue = t
   RowArgs ra = row_args(c, ga, d_g, max_s, max_d, twords, rbeta_packed);
   ra.stage_ent_s = st_s;
   ra.stage_ent_d = st_d;
+  ra.target_ctr = &k->row_next;
+  CK(cudaMemsetAsync(&k->row_next, 0, sizeof(unsigned), c->st));
   ra.sel_bits = sel;
   ra.energy_only = energy_only ? 1 : 0;
   ra.sig_out = sig_out;

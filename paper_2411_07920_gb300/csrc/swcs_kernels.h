@@ -125,7 +125,8 @@ struct RowArgs {
   double* acc;                 // acc[0] += sum c_D sigma_D
   int* err;
   int max_ent_s, max_ent_d;  // capacity of the target's entry lists (all CTAs of its cluster together)
-  int stage_ent_s, stage_ent_d;  // capacity of one CTA's share before the cluster merges them (0: one CTA per target)
+  int stage_ent_s, stage_ent_d;
+  unsigned* target_ctr;  // zeroed before the launch: hands out the targets of one-CTA rows (nullptr: fixed shares)  // capacity of one CTA's share before the cluster merges them (0: one CTA per target)
   int touched_words;  // words of the per-CTA touched-sector bitmap, one bit per 4 entries (0: clear whole rows)
   const uint32_t* sel_bits;  // pool operators to evaluate (nullptr: all)
   // beta single excitations of each grouped determinant, t = occ_slot*nv + vir_slot:

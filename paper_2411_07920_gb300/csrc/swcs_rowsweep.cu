@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(kRowThreads, kMinBlocks)
 row_sweep_kernel(RowArgs A) {
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ RowShared sh;
+  __shared__ int s_next;
   ClusterSync sy{cg::this_cluster()};
   const int crank = (int)sy.cl.block_rank();
   const int gsz = (int)sy.cl.num_blocks();
@@ -60,9 +61,25 @@ row_sweep_kernel(RowArgs A) {
   const int n_sh = (probe || A.energy_only || A.n_shards < 1) ? 1 : A.n_shards;
   const int sh0 = n_sh > 1 ? A.shard : 0;
   const int n_own = n_targets > sh0 ? (n_targets - sh0 + n_sh - 1) / n_sh : 0;
-  for (int jx = cid; jx < n_own; jx += ncl)
-    row_target<kRowThreads>(A, sh, dy, row, sh0 + jx * n_sh, probe, screen, crank, gsz, sy, e_acc, n_lookups,
-                            n_probe_slots, true);  // rows are zeroed before the launch, so a CTA's last clear can go
+  // rows are zeroed before the launch, so the clear of a CTA's last target can be left out (deferred clears)
+  if (gsz == 1 && A.target_ctr) {
+    // one CTA per target: targets handed out in rank order from a counter, so a CTA whose targets were cheap
+    // takes more and the CTAs finish together (a fixed share of 1/152 of the targets each left the last
+    // CTAs working alone for several percent of the launch)
+    for (;;) {
+      __syncthreads();  // every thread has read the previous index
+      if (threadIdx.x == 0) s_next = (int)atomicAdd(A.target_ctr, 1u);
+      __syncthreads();
+      const int jx = s_next;
+      if (jx >= n_own) break;
+      row_target<kRowThreads>(A, sh, dy, row, sh0 + jx * n_sh, probe, screen, crank, gsz, sy, e_acc, n_lookups,
+                              n_probe_slots, true);
+    }
+  } else {
+    for (int jx = cid; jx < n_own; jx += ncl)
+      row_target<kRowThreads>(A, sh, dy, row, sh0 + jx * n_sh, probe, screen, crank, gsz, sy, e_acc, n_lookups,
+                              n_probe_slots, true);
+  }
   row_flush<kRowThreads>(A, sh, e_acc, n_lookups, n_probe_slots);
 }
 
