@@ -334,6 +334,15 @@ int swcs_mlp_grad_dev(swcs_mlp* m, const uint16_t* d_x, const float* d_t, int64_
 int swcs_mlp_train_step_dev(swcs_mlp* m, const uint16_t* d_x, const float* d_t, int64_t n, float lr, double* d_loss);
 int swcs_mlp_activations(swcs_mlp* m, uint16_t* h_H1, uint16_t* h_H2, float* h_y, int64_t n);
 int swcs_mlp_sync(swcs_mlp* m);
+/* Options of the network's training path (no effect on results beyond the
+ * FP32 summation order of the weight gradients):
+ *   "gemm_pipeline"  1 (default): the layer-by-layer GEMMs stream their
+ *              operands by TMA through a ring of shared-memory stages and
+ *              split K over CTAs for the weight gradients, wherever both
+ *              operands admit a tensor map; 0: every GEMM stages its operands
+ *              with plain loads, one K chunk at a time.
+ * Unknown keys or values: SWCS_ERR_INVALID_ARG. */
+int swcs_mlp_set_option(swcs_mlp* m, const char* key, int64_t value);
 int swcs_log_abs_dev(const double* d_g, int64_t n, float* d_t, void* cuda_stream);
 int swcs_pool_features_dev(swcs_ctx* ctx, uint16_t* d_x);
 int swcs_pool_screen_dev(swcs_ctx* ctx, swcs_mlp* m, double frac, int64_t* d_subset, int64_t* h_n_subset);

@@ -28,6 +28,7 @@ struct swcs_mlp {
   float *y = nullptr, *dy = nullptr, *dH1 = nullptr;
   int* err_dev = nullptr;
   int64_t launches = 0;
+  bool pipeline = true;  // option "gemm_pipeline"
 };
 
 namespace {
@@ -94,7 +95,7 @@ bool k_major_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_t ro
 // else through the staged one.  may_split: the FP32 output holds zeros, so K may be split over CTAs.
 int run_gemm(swcs_mlp* m, const GemmArgs& g, bool may_split) {
   CUtensorMap ta, tb;
-  if (g.lda == g.K && g.ldb == g.K && k_major_map(&ta, g.A, (uint64_t)g.K, (uint64_t)g.M, 128) &&
+  if (m->pipeline && g.lda == g.K && g.ldb == g.K && k_major_map(&ta, g.A, (uint64_t)g.K, (uint64_t)g.M, 128) &&
       k_major_map(&tb, g.B, (uint64_t)g.K, (uint64_t)g.N, (uint32_t)g.N)) {
     int splits = 1;
     if (may_split && g.mode == kGemmF32) {
@@ -356,6 +357,18 @@ int swcs_mlp_activations(swcs_mlp* m, uint16_t* h_H1, uint16_t* h_H2, float* h_y
   MCK(cudaMemcpy(&e, m->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
   if (e) return mfail(m, SWCS_ERR_TIMEOUT, "mlp: a tensor-core wait timed out");
   return SWCS_OK;
+}
+
+int swcs_mlp_set_option(swcs_mlp* m, const char* key, int64_t value) {
+  if (!m) return SWCS_ERR_INVALID_ARG;
+  if (!key) return mfail(m, SWCS_ERR_INVALID_ARG, "mlp_set_option: null key");
+  const std::string k(key);
+  if (k == "gemm_pipeline") {
+    if (value != 0 && value != 1) return mfail(m, SWCS_ERR_INVALID_ARG, "gemm_pipeline must be 0 or 1");
+    m->pipeline = value != 0;
+    return SWCS_OK;
+  }
+  return mfail(m, SWCS_ERR_INVALID_ARG, "mlp_set_option: unknown key " + k);
 }
 
 int swcs_mlp_sync(swcs_mlp* m) {

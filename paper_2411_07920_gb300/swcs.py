@@ -87,6 +87,7 @@ _SIGS = {
     "swcs_mlp_train_step_dev": ([_vp, _vp, _vp, _i64, ctypes.c_float, _vp], _i),
     "swcs_mlp_activations": ([_vp, _vp, _vp, _vp, _i64], _i),
     "swcs_mlp_sync": ([_vp], _i),
+    "swcs_mlp_set_option": ([_vp, ctypes.c_char_p, _i64], _i),
     "swcs_log_abs_dev": ([_vp, _i64, _vp, _vp], _i),
     "swcs_pool_features_dev": ([_vp, _vp], _i),
     "swcs_get_sigma": ([_vp, _vp, _vp, _i64, _p64], _i),
@@ -278,6 +279,9 @@ class Mlp:
 
     def sync(self):
         self._ck(lib.swcs_mlp_sync(self._h))
+
+    def set_option(self, key, value):
+        self._ck(lib.swcs_mlp_set_option(self._h, key.encode(), int(value)))
 
     def close(self):
         if getattr(self, "_h", None):

@@ -111,11 +111,13 @@ def within_ulp(gpu, ref, a, w):
     return np.all(np.abs(gpu - ref) <= 2.0 ** -7 * np.abs(ref) + acc)
 
 
+@pytest.mark.parametrize("pipeline", [1, 0])
 @pytest.mark.parametrize("n", [128, 300, 1000])
-def test_forward_stages(S, n):
+def test_forward_stages(S, n, pipeline):
     import torch
     rng = np.random.default_rng(n)
     net = S.Mlp(32, 256)
+    net.set_option("gemm_pipeline", pipeline)
     flat = he_params(rng, 32, 256)
     net.set_params(flat)
     P = unpack(net, flat)
@@ -142,11 +144,15 @@ def test_forward_stages(S, n):
     net.close()
 
 
-@pytest.mark.parametrize("n", [256, 777])
-def test_gradients_match_oracle(S, n):
+@pytest.mark.parametrize("pipeline", [1, 0])
+@pytest.mark.parametrize("n", [256, 777, 5000])
+def test_gradients_match_oracle(S, n, pipeline):
+    """Both GEMM paths (TMA-pipelined with K split over CTAs for the weight gradients; staged with plain
+    loads) within the bounds derived for any FP32 summation order."""
     import torch
     rng = np.random.default_rng(7 + n)
     net = S.Mlp(32, 256)
+    net.set_option("gemm_pipeline", pipeline)
     flat = he_params(rng, 32, 256)
     net.set_params(flat)
     P = unpack(net, flat)
@@ -220,3 +226,63 @@ def test_fused_forward_is_bit_identical(S, n, d_in, width):
     ref = M.forward(x, W1, P["b1"], W2, P["b2"], w3, P["b3"])["y"]
     tol = bound_forward(x, W1, P["b1"], W2, P["b2"], w3) + 2 * U32 * np.abs(ref)
     assert np.all(np.abs(y.cpu().numpy() - ref) <= tol), np.abs(y.cpu().numpy() - ref).max()
+
+
+@pytest.mark.parametrize("n,d_in,width", [(4096, 32, 256), (1000, 64, 128), (333, 32, 64)])
+def test_gemm_paths_agree(S, n, d_in, width):
+    """The forward activations of the two GEMM paths are bit for bit the same (the tensor cores see the same
+    sequence of K = 16 steps); the gradients agree within the bound of two FP32 summation orders."""
+    import torch
+    rng = np.random.default_rng(n + d_in)
+    flat = he_params(rng, d_in, width)
+    x = M.bf16_round(rng.normal(size=(n, d_in)))
+    t = rng.normal(size=n).astype(np.float32)
+    d_x = torch.from_numpy(M.bf16_bits(x).view(np.int16).copy()).cuda()
+    d_t = torch.from_numpy(t).cuda()
+    out = []
+    for pipeline in (1, 0):
+        net = S.Mlp(d_in, width)
+        net.set_option("gemm_pipeline", pipeline)
+        net.set_params(flat)
+        d_g = torch.zeros(net.n_params, dtype=torch.float32, device="cuda")
+        d_loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        net.grad_dev(d_x, d_t, d_g, d_loss)
+        H1b, H2b, y = net.activations(n)
+        out.append((H1b, H2b, y, d_g.cpu().numpy().astype(np.float64), unpack(net, flat)))
+        net.close()
+    (H1a, H2a, ya, ga, P), (H1s, H2s, ys, gs, _) = out
+    assert np.array_equal(H1a, H1s) and np.array_equal(H2a, H2s) and np.array_equal(ya, ys)
+    # every gradient is a sum over the n rows of the batch in an order that atomics or the K split decide:
+    # dW2 = dZ2^T H1 and dW1 = dZ1^T X on the tensor cores, dw3, db3, db2, db1 by FP32 atomics.  Two orders
+    # of the same terms differ by at most 2 gamma(n + 2) sum |terms| (the + 2 covers the FP32 products with dy;
+    # |dZ| is bounded from above, the BF16 rounding of dZ2 and dZ1 adding at most 2^-8 each)
+    H1, H2 = M.from_bf16_bits(H1a), M.from_bf16_bits(H2a)
+    W2, w3 = M.bf16_round(P["W2"]), M.bf16_round(P["w3"])
+    dy = np.abs(2.0 * (ya.astype(np.float64) - t) / n) * (1 + 2.0 ** -20)
+    adZ2 = np.outer(dy, np.abs(w3)) * (H2 > 0) * (1 + 2.0 ** -7)
+    adZ1 = (adZ2 @ np.abs(W2)) * (H1 > 0) * (1 + 2.0 ** -7)
+    G = 2 * gamma(n + 2)
+    bound = {"W2": G * (adZ2.T @ np.abs(H1)), "W1": G * (adZ1.T @ np.abs(x)), "w3": G * (dy @ np.abs(H2)),
+             "b3": G * dy.sum(), "b2": G * adZ2.sum(axis=0), "b1": G * adZ1.sum(axis=0)}
+    A, Sg = unpack_grad(P, ga), unpack_grad(P, gs)
+    for name in A:
+        assert np.all(np.abs(A[name] - Sg[name]) <= bound[name] + 1e-30), (name, np.abs(A[name] - Sg[name]).max())
+
+
+def unpack_grad(P, g):
+    """The gradient vector cut like the parameter dictionary P."""
+    out, o = {}, 0
+    for name in ("W1", "b1", "W2", "b2", "w3", "b3"):
+        k = int(np.asarray(P[name]).size)
+        out[name] = g[o:o + k].reshape(np.asarray(P[name]).shape)
+        o += k
+    return out
+
+
+def test_mlp_option_errors(S):
+    net = S.Mlp(32, 256)
+    with pytest.raises(Exception):
+        net.set_option("gemm_pipeline", 2)
+    with pytest.raises(Exception):
+        net.set_option("no_such_option", 1)
+    net.close()
