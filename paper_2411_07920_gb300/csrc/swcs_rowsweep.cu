@@ -51,11 +51,11 @@ row_sweep_kernel(RowArgs A) {
   double e_acc = 0.0;
   unsigned n_lookups = 0, n_probe_slots = 0;  // hash-probe counters (when requested)
 
-  // targets: every alpha string of the sector, in energy-only mode the alpha strings of the state's
-  // groups (the others hold no determinant whose sigma is read back), in probe mode the listed ones
+  // targets: every alpha string of the sector in colex order (in energy-only mode those that hold no
+  // determinant of the state return at once: nothing of theirs is read back), in probe mode the listed ones
   const bool probe = A.n_probe > 0;
   const bool screen = A.screen && A.sel_bits && dy.touched && !probe && !A.energy_only;
-  const int n_targets = probe ? A.n_probe : A.energy_only ? (int)*A.n_groups : A.NA;
+  const int n_targets = probe ? A.n_probe : A.NA;
   // a shard of the pool sweep visits the alpha strings xi = shard (mod n_shards) only (alpha_list is in
   // colex order, so xi is the string's rank)
   const int n_sh = (probe || A.energy_only || A.n_shards < 1) ? 1 : A.n_shards;

@@ -695,8 +695,7 @@ __device__ void row_target(const RowArgs& A, RowShared& sh, const RowDyn& dy, do
   const int nwords = A.touched_words;
   const bool merged = A.stage_ent_s > 0;  // the cluster merges its CTAs' entries (clusters of 2 or more)
   (void)n_to;
-  const uint32_t X = probe ? __ldg(&A.probe_x[xi])
-                           : A.energy_only ? even_bits(__ldg(&A.gkey[A.goff[xi]])) : A.alpha_list[xi];
+  const uint32_t X = probe ? __ldg(&A.probe_x[xi]) : A.alpha_list[xi];
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     const bool inr = lane < m;
@@ -709,7 +708,7 @@ __device__ void row_target(const RowArgs& A, RowShared& sh, const RowDyn& dy, do
     if (lane == 0) {
       sh.n_s_loc = 0;
       sh.n_d_loc = 0;
-      const int64_t g = A.energy_only ? (int64_t)xi : idx_lookup(A.atab, A.amask, (uint64_t)X);
+      const int64_t g = idx_lookup(A.atab, A.amask, (uint64_t)X);
       sh.gx_off = g >= 0 ? A.goff[g] : 0;
       sh.gx_cnt = g >= 0 ? A.goff[g + 1] - A.goff[g] : 0;
     }
