@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kRowThreads, kMinBlocks)
 row_sweep_kernel(RowArgs A) {
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ RowShared sh;
-  __shared__ int s_next;
+  __shared__ int s_next[2];
   ClusterSync sy{cg::this_cluster()};
   const int crank = (int)sy.cl.block_rank();
   const int gsz = (int)sy.cl.num_blocks();
@@ -62,16 +62,19 @@ row_sweep_kernel(RowArgs A) {
   const int sh0 = n_sh > 1 ? A.shard : 0;
   const int n_own = n_targets > sh0 ? (n_targets - sh0 + n_sh - 1) / n_sh : 0;
   // rows are zeroed before the launch, so the clear of a CTA's last target can be left out (deferred clears)
-  if (gsz == 1 && A.target_ctr) {
-    // one CTA per target: targets handed out in rank order from a counter, so a CTA whose targets were cheap
-    // takes more and the CTAs finish together (a fixed share of 1/152 of the targets each left the last
-    // CTAs working alone for several percent of the launch)
-    for (;;) {
-      __syncthreads();  // every thread has read the previous index
-      if (threadIdx.x == 0) s_next = (int)atomicAdd(A.target_ctr, 1u);
-      __syncthreads();
-      const int jx = s_next;
-      if (jx >= n_own) break;
+  if (A.target_ctr) {
+    // targets handed out in rank order from a counter, so a CTA (or cluster) whose targets were cheap takes
+    // more and all finish together (a fixed share of the targets each left the last ones working alone for
+    // several percent of the launch).  The cluster's first CTA takes the index and every CTA reads it there;
+    // the two slots alternate, so a slot is rewritten only after the barriers of the target that read it.
+    for (int it = 0;; ++it) {
+      if (crank == 0 && threadIdx.x == 0) s_next[it & 1] = (int)atomicAdd(A.target_ctr, 1u);
+      sy.sync();
+      const int jx = *sy.remote(&s_next[it & 1], 0);
+      if (jx >= n_own) {
+        sy.sync();  // no CTA leaves while another still reads its shared memory
+        break;
+      }
       row_target<kRowThreads>(A, sh, dy, row, sh0 + jx * n_sh, probe, screen, crank, gsz, sy, e_acc, n_lookups,
                               n_probe_slots, true);
     }
